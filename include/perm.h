@@ -1,0 +1,136 @@
+/*
+ * perm.h - C ABI of the GB300 permanent library (libperm.so).
+ *
+ * The library evaluates the permanent of an n x n matrix,
+ *
+ *     perm(A) = sum over permutations sigma of prod_i a_{i,sigma(i)}      (Eq. 1)
+ *
+ * with Ryser's inclusion-exclusion formula (Eq. 2) in the Nijenhuis-Wilf form
+ * (Eq. nwx): a row vector x, started at x_i = a_{i,n} - r_i/2, is updated by
+ * one column per step while the 2^(n-1) column subsets of columns 1..n-1 are
+ * visited in binary-reflected Gray-code order, Gray_g = g xor (g >> 1)
+ * (Sec. 2, Table 1, Alg. 1); every step adds (-1)^g prod_i x_i to a sum and
+ * perm(A) = 2 (-1)^(n-1) times the sum.  The 2^(n-1) steps are split into
+ * aligned chunks of 2^c steps (Alg. 3, with the power-of-two chunks of
+ * Sec. 3.1.1), each started from the x of its first Gray code, and the chunk
+ * sums are reduced on the device.
+ *
+ * Conventions for every entry point:
+ *   - Matrices are row-major, a_{i,j} at A[i*n + j], 0-based; the paper's
+ *     column n is column n-1 here.
+ *   - "device" pointers are CUDA device (or managed) memory on the current
+ *     device; "host" pointers are ordinary host memory.  The caller owns every
+ *     buffer; the library never frees or keeps a caller pointer.
+ *   - stream is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Device-pointer calls are stream-ordered and return without waiting for
+ *     the GPU; they take their scratch memory with cudaMallocAsync on that
+ *     stream and release it with cudaFreeAsync on the same stream.
+ *   - The return value is a perm_status_t for errors found on the host
+ *     (argument checks, CUDA launch errors).  Errors that depend on the matrix
+ *     values are found on the GPU and written to *status (device int32,
+ *     optional: pass NULL to skip it) when the call completes on the stream.
+ *   - n ranges over 0..63 (n_max = 63 as in Sec. 3.2); perm of the 0 x 0
+ *     matrix is 1.
+ *   - No call traps, aborts or prints; nothing is thrown across the ABI.
+ */
+#ifndef PERM_H
+#define PERM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PERM_ABI_VERSION 1
+#define PERM_NMAX 63
+
+typedef enum {
+  PERM_F64 = 0,  /* real binary64 entries                                   */
+  PERM_C128 = 1, /* complex entries, (re, im) binary64 pairs                 */
+  PERM_BIN = 2   /* 0/1 entries as uint8; the result is exact               */
+} perm_type_t;
+
+typedef enum {
+  PERM_OK = 0,
+  PERM_EINVAL = 1,    /* bad argument; non-finite entry; a BIN entry not 0/1 */
+  PERM_ERANGE = 2,    /* n out of 0..63, range out of [0, 2^(n-1)), or a
+                         binary64 result that can overflow                      */
+  PERM_EOVERFLOW = 3, /* BIN: the permanent may not fit 128 bits              */
+  PERM_ECUDA = 4,     /* a CUDA call failed                                    */
+  PERM_ENOMEM = 5     /* scratch allocation failed                             */
+} perm_status_t;
+
+/*
+ * perm - permanent of one dense n x n matrix (Eq. 1 by Alg. 1 + Alg. 3).
+ *
+ *   A      device; PERM_F64: double[n*n]; PERM_C128: double[2*n*n] as (re, im)
+ *          pairs; PERM_BIN: uint8_t[n*n] holding only 0 and 1.
+ *   out    device; PERM_F64: double[1]; PERM_C128: double[2] = (re, im);
+ *          PERM_BIN: uint64_t[2] = the permanent as a little-endian unsigned
+ *          128-bit integer.
+ *   status device int32_t[1] or NULL; receives PERM_OK, PERM_EINVAL (a
+ *          non-finite entry, or a BIN entry other than 0/1: out is then NaN /
+ *          zero), PERM_ERANGE (PERM_F64/C128 only: the largest possible term
+ *          exceeds the binary64 range; out is then NaN) or PERM_EOVERFLOW
+ *          (PERM_BIN only: perm(A) may be >= 2^128; out is then zero).
+ *
+ * Real and complex entries are converted once to 64-bit fixed point with a
+ * power-of-two scale per row (error at most 2^-60 of the row's absolute sum)
+ * and the row vector x is kept exactly; products carry 62-bit mantissas and
+ * the signed sum is accumulated in binary64 with a double-double carry.
+ * Binary matrices run in exact wrap-around integer arithmetic (192 bits).
+ * Results are bitwise reproducible for a given n, type and GPU model.
+ */
+int perm(const void* A, int n, int type, void* out, int32_t* status, void* stream);
+
+/*
+ * perm_range - unscaled partial sum of the steps g in [g_begin, g_end)
+ * (0 <= g_begin <= g_end <= 2^(n-1)), so that ranges can be spread over GPUs,
+ * processes or time (Secs. 3.3 and 6.3: the iteration space is split first per GPU;
+ * the only exchange is the final sum).
+ *
+ *   partial device;
+ *     PERM_F64:  double[2]   = (hi, lo) of  sum_g (-1)^g prod_i x_i(g);
+ *     PERM_C128: double[4]   = (re hi, re lo, im hi, im lo) of the same sum;
+ *     PERM_BIN:  uint64_t[3] = sum_g (-1)^g prod_i x'_i(g) modulo 2^192,
+ *                little-endian, with the doubled integer rows x' = 2x.
+ *   x_i(g) is Alg. 1's row vector after the subsets up to Gray_g, with
+ *   x_i(0) = a_{i,n-1} - (sum_j a_{i,j}) / 2.
+ *   status as for perm(); for PERM_BIN it reports PERM_EOVERFLOW when the
+ *   combined sum may not determine perm(A) (the partial itself stays exact).
+ */
+int perm_range(const void* A, int n, int type, uint64_t g_begin, uint64_t g_end, void* partial,
+               int32_t* status, void* stream);
+
+/*
+ * perm_combine - host-side reduction of perm_range partials that together
+ * cover [0, 2^(n-1)) exactly once, in the order given, into the perm() output
+ * format: multiply by 2 (-1)^(n-1) (Alg. 1) for real and complex; for BIN add
+ * modulo 2^192, check that the low n-1 bits are zero (PERM_EINVAL otherwise),
+ * shift them out, apply (-1)^(n-1) and check the value fits 128 bits
+ * (PERM_EOVERFLOW otherwise).
+ *
+ *   partials host, count consecutive partials of the perm_range layout.
+ *   out      host, the perm() layout.
+ */
+int perm_combine(int type, int n, const void* partials, int count, void* out);
+
+/*
+ * perm_host - perm() on host buffers: copies A in, runs perm() on stream,
+ * copies the result out and waits.  Returns the device status as well.
+ *   A_host   host, layout as perm()'s A;  out_host  host, layout as perm()'s out.
+ */
+int perm_host(const void* A_host, int n, int type, void* out_host, void* stream);
+
+/* Human-readable name of a perm_status_t; never NULL. */
+const char* perm_status_string(int status);
+
+/* PERM_ABI_VERSION of the loaded library. */
+int perm_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PERM_H */

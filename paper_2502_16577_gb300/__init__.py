@@ -1,0 +1,179 @@
+"""GB300 permanents: Ryser / Nijenhuis-Wilf Gray-code sweep on sm_103a.
+
+A thin Python binding of libperm.so (include/perm.h).  Every step of the
+computation runs in the library's CUDA kernels; this module only moves
+pointers, sizes and results.  PyTorch supplies device memory and streams.
+
+    import torch, paper_2502_16577_gb300 as pg
+    A = torch.rand(24, 24, dtype=torch.float64, device="cuda")
+    pg.perm(A)                       # float
+    pg.perm(U_complex128)            # complex
+    pg.perm(B_uint8)                 # int, exact
+    pg.perm_range(A, g0, g1)         # raw partial of steps [g0, g1)
+    pg.perm_combine(A_type, n, [..]) # host reduction of partials
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import PERM_BIN, PERM_C128, PERM_F64, PermError, check, load
+
+__all__ = ["perm", "perm_async", "perm_range", "perm_combine", "perm_host", "perm_type_of", "PermError",
+           "PERM_F64", "PERM_C128", "PERM_BIN", "load"]
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+def perm_type_of(dtype) -> int:
+    torch = _torch()
+    if dtype in (torch.float64,):
+        return PERM_F64
+    if dtype in (torch.complex128,):
+        return PERM_C128
+    if dtype in (torch.uint8, torch.bool):
+        return PERM_BIN
+    raise TypeError(f"unsupported dtype {dtype}: use float64, complex128 or uint8 (0/1)")
+
+
+def _as_device_matrix(A):
+    torch = _torch()
+    if not isinstance(A, torch.Tensor) or not A.is_cuda:
+        raise TypeError("A must be a CUDA torch.Tensor (use perm_host for host arrays)")
+    if A.dim() != 2 or A.shape[0] != A.shape[1]:
+        raise ValueError("A must be a square matrix")
+    if A.dtype == torch.bool:
+        A = A.to(torch.uint8)
+    return A.contiguous()
+
+
+def _stream_handle(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream), s
+
+
+def _out_buffers(t: int, device, words: int):
+    torch = _torch()
+    if t == PERM_BIN:
+        out = torch.zeros(words, dtype=torch.int64, device=device)
+    else:
+        out = torch.zeros(words, dtype=torch.float64, device=device)
+    status = torch.full((1,), -1, dtype=torch.int32, device=device)
+    return out, status
+
+
+def _u(words) -> int:
+    v = 0
+    for i, w in enumerate(words):
+        v |= (int(w) & 0xFFFFFFFFFFFFFFFF) << (64 * i)
+    return v
+
+
+def perm_async(A, out, status=None, stream=None) -> None:
+    """Enqueue perm(A) on a stream without waiting; out / status are device tensors
+    (float64[1], float64[2] for complex, int64[2] for 0/1; int32[1])."""
+    lib = load()
+    A = _as_device_matrix(A)
+    t = perm_type_of(A.dtype)
+    h, _ = _stream_handle(stream)
+    rc = lib.perm(ctypes.c_void_p(A.data_ptr()), A.shape[0], t, ctypes.c_void_p(out.data_ptr()),
+                  ctypes.c_void_p(status.data_ptr() if status is not None else 0), h)
+    check(rc, "perm")
+
+
+def perm(A, stream=None):
+    """Permanent of a square CUDA tensor: float64 -> float, complex128 -> complex,
+    uint8/bool 0/1 -> exact int.  Waits for the result."""
+    A = _as_device_matrix(A)
+    t = perm_type_of(A.dtype)
+    out, status = _out_buffers(t, A.device, 1 if t == PERM_F64 else 2)
+    perm_async(A, out, status, stream)
+    _, s = _stream_handle(stream)
+    s.synchronize()
+    check(int(status.item()), "perm")
+    o = out.cpu().numpy()
+    if t == PERM_F64:
+        return float(o[0])
+    if t == PERM_C128:
+        return complex(float(o[0]), float(o[1]))
+    return _u(o)
+
+
+def perm_range(A, g_begin: int, g_end: int, stream=None):
+    """Raw partial over steps [g_begin, g_end): (hi, lo) for float64,
+    (re_hi, re_lo, im_hi, im_lo) for complex128, an int mod 2^192 for 0/1."""
+    lib = load()
+    A = _as_device_matrix(A)
+    t = perm_type_of(A.dtype)
+    words = {PERM_F64: 2, PERM_C128: 4, PERM_BIN: 3}[t]
+    out, status = _out_buffers(t, A.device, words)
+    h, s = _stream_handle(stream)
+    rc = lib.perm_range(ctypes.c_void_p(A.data_ptr()), A.shape[0], t, int(g_begin), int(g_end),
+                        ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(status.data_ptr()), h)
+    check(rc, "perm_range")
+    s.synchronize()
+    st = int(status.item())
+    o = out.cpu().numpy()
+    if t == PERM_BIN:
+        if st not in (_lib.PERM_OK, _lib.PERM_EOVERFLOW):
+            check(st, "perm_range")
+        return _u(o)
+    check(st, "perm_range")
+    return tuple(float(v) for v in o)
+
+
+def perm_combine(t: int, n: int, partials):
+    """Host-side reduction of perm_range partials covering [0, 2^(n-1))."""
+    lib = load()
+    if t == PERM_BIN:
+        arr = np.zeros((len(partials), 3), dtype=np.uint64)
+        for i, v in enumerate(partials):
+            v = int(v) % (1 << 192)
+            for w in range(3):
+                arr[i, w] = (v >> (64 * w)) & 0xFFFFFFFFFFFFFFFF
+        out = np.zeros(2, dtype=np.uint64)
+    else:
+        width = 2 if t == PERM_F64 else 4
+        arr = np.ascontiguousarray(np.asarray(partials, dtype=np.float64).reshape(len(partials), width))
+        out = np.zeros(1 if t == PERM_F64 else 2, dtype=np.float64)
+    rc = lib.perm_combine(t, n, arr.ctypes.data_as(ctypes.c_void_p), len(partials), out.ctypes.data_as(ctypes.c_void_p))
+    check(rc, "perm_combine")
+    if t == PERM_F64:
+        return float(out[0])
+    if t == PERM_C128:
+        return complex(float(out[0]), float(out[1]))
+    return _u(out)
+
+
+def perm_host(A, stream=None):
+    """perm() on a host numpy array (copies in and out inside the library)."""
+    lib = load()
+    A = np.asarray(A)
+    if A.ndim != 2 or A.shape[0] != A.shape[1]:
+        raise ValueError("A must be a square matrix")
+    if np.iscomplexobj(A):
+        t, A = PERM_C128, np.ascontiguousarray(A, dtype=np.complex128)
+        out = np.zeros(2, dtype=np.float64)
+    elif A.dtype in (np.uint8, np.bool_):
+        t, A = PERM_BIN, np.ascontiguousarray(A, dtype=np.uint8)
+        out = np.zeros(2, dtype=np.uint64)
+    else:
+        t, A = PERM_F64, np.ascontiguousarray(A, dtype=np.float64)
+        out = np.zeros(1, dtype=np.float64)
+    h = ctypes.c_void_p(0)
+    if stream is not None:
+        h = ctypes.c_void_p(stream.cuda_stream)
+    rc = lib.perm_host(A.ctypes.data_as(ctypes.c_void_p), A.shape[0], t, out.ctypes.data_as(ctypes.c_void_p), h)
+    check(rc, "perm_host")
+    if t == PERM_F64:
+        return float(out[0])
+    if t == PERM_C128:
+        return complex(float(out[0]), float(out[1]))
+    return _u(out)

@@ -1,0 +1,69 @@
+"""ctypes loader of libperm.so (the C ABI in include/perm.h).
+
+Argument marshalling only.  The library is built in-tree by build.py; when it
+is missing this module raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+PERM_F64, PERM_C128, PERM_BIN = 0, 1, 2
+PERM_OK, PERM_EINVAL, PERM_ERANGE, PERM_EOVERFLOW, PERM_ECUDA, PERM_ENOMEM = range(6)
+
+_vp = ctypes.c_void_p
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_lib = None
+
+SYMBOLS = ("perm", "perm_range", "perm_combine", "perm_host", "perm_status_string", "perm_abi_version")
+
+
+class PermError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = int(code)
+        super().__init__(f"{what}: {status_string(code)}" if what else status_string(code))
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libperm.so.  Raises if it was not built (no fallback path exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = lib_path()
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise ImportError(f"libperm.so not built ({path}); run paper_2502_16577_gb300.build.build()")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    lib.perm.restype = ctypes.c_int
+    lib.perm.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp]
+    lib.perm_range.restype = ctypes.c_int
+    lib.perm_range.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, _vp, _vp, _vp]
+    lib.perm_combine.restype = ctypes.c_int
+    lib.perm_combine.argtypes = [ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, _vp]
+    lib.perm_host.restype = ctypes.c_int
+    lib.perm_host.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp]
+    lib.perm_status_string.restype = ctypes.c_char_p
+    lib.perm_status_string.argtypes = [ctypes.c_int]
+    lib.perm_abi_version.restype = ctypes.c_int
+    lib.perm_abi_version.argtypes = []
+    _lib = lib
+    return lib
+
+
+def status_string(code: int) -> str:
+    try:
+        return load().perm_status_string(int(code)).decode()
+    except ImportError:
+        return f"status {code}"
+
+
+def check(code: int, what: str = "") -> None:
+    if int(code) != PERM_OK:
+        raise PermError(code, what)

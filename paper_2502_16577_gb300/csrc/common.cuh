@@ -1,0 +1,135 @@
+// Shared device helpers of the permanent kernels (GB300, sm_103a).
+//
+// Nothing here is specific to one element type: double-double accumulation
+// (Knuth's TwoSum, the "quad as two doubles" outer sum of Sec. 5), warp and
+// block reductions in a fixed order, the launch argument block, and the
+// integer helpers of the fixed-point product.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "perm.h"
+
+namespace permgpu {
+
+constexpr int kBlock = 256;  // threads per CTA for every Ryser kernel
+constexpr int kWarps = kBlock / 32;
+
+// ----------------------------------------------------------- double-double
+
+struct dd {
+  double hi, lo;
+};
+
+__device__ __forceinline__ dd dd_make(double s, double e) {
+  double h = s + e;
+  dd r;
+  r.lo = e - (h - s);
+  r.hi = h;
+  return r;
+}
+
+__device__ __forceinline__ dd dd_add(dd a, dd b) {
+  double s = a.hi + b.hi;
+  double bv = s - a.hi;
+  double e = (a.hi - (s - bv)) + (b.hi - bv);
+  e += a.lo + b.lo;
+  return dd_make(s, e);
+}
+
+__device__ __forceinline__ dd dd_add_d(dd a, double b) {
+  double s = a.hi + b;
+  double bv = s - a.hi;
+  double e = (a.hi - (s - bv)) + (b - bv);
+  e += a.lo;
+  return dd_make(s, e);
+}
+
+__device__ __forceinline__ dd dd_shfl_down(dd v, int off) {
+  dd r;
+  r.hi = __shfl_down_sync(0xffffffffu, v.hi, off);
+  r.lo = __shfl_down_sync(0xffffffffu, v.lo, off);
+  return r;
+}
+
+// Fixed-order warp reduction (lane 0 holds the result).
+__device__ __forceinline__ dd dd_warp_sum(dd v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v = dd_add(v, dd_shfl_down(v, off));
+  return v;
+}
+
+// ------------------------------------------------------------ launch block
+
+// Arguments of one Ryser launch.  The chunk grid: chunk k covers steps
+// g in [k 2^c, (k+1) 2^c); chunks [k_begin, k_begin + nchunks) are visited and
+// only steps inside [g_begin, g_end) are accumulated.
+struct RyserArgs {
+  const void* A;      // element type given by the kernel
+  int n;
+  int c;              // log2 of the chunk length, 0..30
+  int mode;           // 0: write the finished permanent, 1: write the raw range sum
+  int one;            // always 1 (a multiplier the compiler cannot fold away)
+  uint64_t g_begin, g_end;
+  uint64_t k_begin, nchunks;
+  void* part;         // per-CTA partials (scratch, gridDim.x entries)
+  unsigned int* counter;  // arrival counter (scratch, zero before launch)
+  void* out;
+  int32_t* status;    // optional device status word
+};
+
+// Gray code of step g (Sec. 2): bit j set <=> column j is in the subset.
+__device__ __forceinline__ uint64_t gray64(uint64_t g) { return g ^ (g >> 1); }
+
+// Step window of chunk k inside [g_begin, g_end): local t in [tlo, tlo + tcnt).
+__device__ __forceinline__ void chunk_window(const RyserArgs& a, uint64_t g0, bool active, uint32_t& tlo,
+                                             uint32_t& tcnt) {
+  uint64_t len = 1ull << a.c;
+  uint64_t lo = a.g_begin > g0 ? a.g_begin - g0 : 0;
+  uint64_t hi = a.g_end > g0 ? a.g_end - g0 : 0;
+  if (hi > len) hi = len;
+  tlo = (uint32_t)lo;
+  tcnt = (active && hi > lo) ? (uint32_t)(hi - lo) : 0u;
+}
+
+// Arrival protocol of the last CTA: every CTA stores its partial, the last one
+// to arrive reads them all in index order.  Returns true in the last CTA.
+__device__ __forceinline__ bool arrive_last(unsigned int* counter) {
+  __shared__ unsigned int s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    unsigned int prev = atomicAdd(counter, 1u);
+    s_last = (prev == gridDim.x - 1) ? 1u : 0u;
+  }
+  __syncthreads();
+  if (s_last) __threadfence();
+  return s_last != 0;
+}
+
+// Block-wide dd reduction (fixed order); result valid in thread 0.
+__device__ __forceinline__ dd dd_block_sum(dd v) {
+  __shared__ dd s_w[kWarps];
+  v = dd_warp_sum(v);
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) s_w[w] = v;
+  __syncthreads();
+  dd r = {0.0, 0.0};
+  if (w == 0) {
+    r = lane < kWarps ? s_w[lane] : dd{0.0, 0.0};
+    r = dd_warp_sum(r);
+  }
+  __syncthreads();
+  return r;
+}
+
+// Fixed-order sum of count dd partials by warp 0 (lane-strided, then tree).
+__device__ __forceinline__ dd dd_sum_partials(const dd* p, int count) {
+  dd r = {0.0, 0.0};
+  int lane = threadIdx.x & 31;
+  for (int i = lane; i < count; i += 32) r = dd_add(r, p[i]);
+  return dd_warp_sum(r);
+}
+
+}  // namespace permgpu

@@ -1,0 +1,264 @@
+// Dense complex Ryser kernel (Alg. 1 over complex entries, chunked as Alg. 3
+// with power-of-two chunks, Sec. 3.1.1).
+//
+// Rows are scaled by a power of two per row (taken from sum_j |re| + |im|) and
+// rounded once to 64-bit fixed point, so the doubled row vector x' = 2x is an
+// exact pair of int64 per row.  The running product z = prod_i x'_i keeps a
+// shared exponent for its real and imaginary parts, both held as signed
+// 62-bit integers split into a signed high limb and a 31-bit low limb, so
+// that every partial product is a signed 32x32->64 multiply-add with no sign
+// handling:  (p1 2^31 + p0)(y1 2^31 + y0) = p1 y1 2^62 + (p1 y0 + p0 y1) 2^31 + ...
+// After each complex multiply the pair is renormalised so that the larger part
+// has its top bit at 2^60.  Terms are rounded once to binary64 (the
+// conversion runs on the otherwise idle FP64 pipe), summed over 8 steps and
+// carried into double-double lane partials (Sec. 5).
+#pragma once
+
+#include "common.cuh"
+
+namespace permgpu {
+
+struct CProd {
+  int32_t r1, i1;    // signed high limbs (bits 31..62)
+  uint32_t r0, i0;   // low 31-bit limbs
+};
+
+__device__ __forceinline__ void cprod_init(CProd& p) {
+  p.r1 = 1 << 29;  // 2^60 (real part), imaginary part 0
+  p.r0 = 0u;
+  p.i1 = 0;
+  p.i0 = 0u;
+}
+
+// p <- p * y for y = (yr, yi) signed with |yr|, |yi| < 2^61.  Returns the
+// renormalising shift s (the product was multiplied by 2^(s-62)).
+__device__ __forceinline__ int cprod_mul(CProd& p, long long yr, long long yi) {
+  const int32_t yr1 = (int32_t)(yr >> 31), yi1 = (int32_t)(yi >> 31);
+  const int32_t yr0 = (int32_t)((uint32_t)yr & 0x7FFFFFFFu), yi0 = (int32_t)((uint32_t)yi & 0x7FFFFFFFu);
+  const int32_t nr0 = (int32_t)p.r0, ni0 = (int32_t)p.i0;
+  // middle partial products (scale 2^31), |t| < 2^63
+  long long tr = (long long)p.r1 * yr0 + (long long)nr0 * yr1 - (long long)p.i1 * yi0 - (long long)ni0 * yi1;
+  long long ti = (long long)p.r1 * yi0 + (long long)nr0 * yi1 + (long long)p.i1 * yr0 + (long long)ni0 * yr1;
+  // high partial products (scale 2^62) plus the carried middle part
+  long long vr = (long long)p.r1 * yr1 - (long long)p.i1 * yi1 + (tr >> 31);
+  long long vi = (long long)p.r1 * yi1 + (long long)p.i1 * yr1 + (ti >> 31);
+  // top set bit of max(|vr|, |vi|) (ones' complement magnitude of the high words)
+  const uint32_t hr = (uint32_t)((unsigned long long)vr >> 32), hi = (uint32_t)((unsigned long long)vi >> 32);
+  const uint32_t w = (hr ^ (uint32_t)((int32_t)hr >> 31)) | (hi ^ (uint32_t)((int32_t)hi >> 31));
+  int pos;
+  asm("bfind.u32 %0, %1;" : "=r"(pos) : "r"(w));  // -1 when w == 0
+  // shift so that the top bit lands at 2^60 (bit 28 of the high word)
+  const int s = 28 - pos;  // in [0, 29]; 29 when both parts are tiny
+  const long long nr = vr << s, ni = vi << s;
+  p.r1 = (int32_t)(nr >> 31);
+  p.r0 = (uint32_t)nr & 0x7FFFFFFFu;
+  p.i1 = (int32_t)(ni >> 31);
+  p.i0 = (uint32_t)ni & 0x7FFFFFFFu;
+  return s;
+}
+
+template <int N>
+struct CplxLayout {
+  static constexpr int NCOL = N > 1 ? N - 1 : 0;
+  // D[(2j + s) * N + i] as (re, im) longlong2, then base[N], then zero[N]
+  static constexpr size_t kD = 0;
+  static constexpr size_t kBase = kD + sizeof(longlong2) * 2 * NCOL * N;
+  static constexpr size_t kZero = kBase + sizeof(longlong2) * N;
+  static constexpr size_t kBytes = kZero + sizeof(longlong2) * N;
+};
+
+struct CplxShared {
+  int sum_s;
+  int bound_log2;
+  int nonfinite;
+  int zero_row;
+};
+
+// Q_ij = round(a_ij 2^s_i) (both parts), s_i = 60 - k_i with
+// sum_j |re| + |im| in [2^(k_i-1), 2^k_i): |Y_i| <= 2^60 per part.
+template <int N>
+__device__ __forceinline__ void cplx_stage(const double* __restrict__ A, unsigned char* smem, CplxShared& sh) {
+  using Lo = CplxLayout<N>;
+  longlong2* D = reinterpret_cast<longlong2*>(smem + Lo::kD);
+  longlong2* base = reinterpret_cast<longlong2*>(smem + Lo::kBase);
+  longlong2* zero = reinterpret_cast<longlong2*>(smem + Lo::kZero);
+  if (threadIdx.x == 0) {
+    sh.sum_s = 0;
+    sh.bound_log2 = 0;
+    sh.nonfinite = 0;
+    sh.zero_row = 0;
+  }
+  __syncthreads();
+  int i = threadIdx.x;
+  if (i < N) {
+    const double* row = A + 2 * (size_t)i * N;
+    double absum = 0.0;
+    int fin = 1;
+    for (int j = 0; j < 2 * N; ++j) {
+      double v = row[j];
+      fin &= isfinite(v) ? 1 : 0;
+      absum += fabs(v);
+    }
+    int k = 0;
+    if (fin && absum > 0.0) frexp(absum, &k);
+    const int s = 60 - k;
+    long long sr = 0, si = 0;
+    for (int j = 0; j < N - 1; ++j) {
+      long long qr = fin ? __double2ll_rn(ldexp(row[2 * j], s)) : 0;
+      long long qi = fin ? __double2ll_rn(ldexp(row[2 * j + 1], s)) : 0;
+      sr += qr;
+      si += qi;
+      D[(2 * j) * N + i] = make_longlong2(2 * qr, 2 * qi);
+      D[(2 * j + 1) * N + i] = make_longlong2(-2 * qr, -2 * qi);
+    }
+    long long nr = fin ? __double2ll_rn(ldexp(row[2 * (N - 1)], s)) : 0;
+    long long ni = fin ? __double2ll_rn(ldexp(row[2 * (N - 1) + 1], s)) : 0;
+    base[i] = make_longlong2(nr - sr, ni - si);
+    zero[i] = make_longlong2(0, 0);
+    atomicAdd(&sh.sum_s, s);
+    atomicAdd(&sh.bound_log2, k - 1);
+    if (!fin) atomicOr(&sh.nonfinite, 1);
+    if (fin && absum == 0.0) atomicOr(&sh.zero_row, 1);
+  }
+  __syncthreads();
+}
+
+template <int N>
+__global__ void __launch_bounds__(kBlock, (N <= 8 ? 2 : 1)) ryser_cplx_kernel(RyserArgs a) {
+  using Lo = CplxLayout<N>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ CplxShared sh;
+  cplx_stage<N>(static_cast<const double*>(a.A), smem, sh);
+  const longlong2* D = reinterpret_cast<const longlong2*>(smem + Lo::kD);
+  const longlong2* base = reinterpret_cast<const longlong2*>(smem + Lo::kBase);
+  const longlong2* zero = reinterpret_cast<const longlong2*>(smem + Lo::kZero);
+  const bool bad = sh.nonfinite || sh.bound_log2 + N > 1000;
+  const bool skip = bad || sh.zero_row;
+  // Each chain starts at 2^60 (= 1) and every one of the N + 1 multiplies
+  // (N rows, then the merge of the two chains) scales by 2^(s - 62), so
+  // prod_i Y_i = z 2^(62 (N+1) - 120 - sum shifts), and with Y_i = 2 x_i 2^s_i
+  // the term prod_i x_i = z 2^(ebase - sum shifts).
+  const int ebase = 62 * (N + 1) - 120 - sh.sum_s - N;
+
+  dd accr = {0.0, 0.0}, acci = {0.0, 0.0};
+  const int lane = threadIdx.x & 31;
+  const uint64_t warp_id = (uint64_t)(blockIdx.x * kBlock + threadIdx.x) >> 5;
+  const uint64_t nwarps = (uint64_t)(gridDim.x * kBlock) >> 5;
+  const uint64_t ngroups = skip ? 0 : (a.nchunks + 31) / 32;
+  const uint32_t nsteps = 1u << a.c;
+
+  for (uint64_t q = warp_id; q < ngroups; q += nwarps) {
+    const uint64_t kk = q * 32 + lane;
+    const bool active = kk < a.nchunks;
+    const uint64_t k = a.k_begin + kk;
+    const uint64_t g0 = k << a.c;
+    uint32_t tlo, tcnt;
+    chunk_window(a, g0, active, tlo, tcnt);
+    const uint32_t kb = (uint32_t)(k & 1u) << a.c;
+    const uint32_t gpar = (uint32_t)(g0 & 1u);
+
+    long long Yr[N], Yi[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      Yr[i] = base[i].x;
+      Yi[i] = base[i].y;
+    }
+    const uint64_t G = gray64(g0);
+    for (int j = (a.c > 0 ? a.c - 1 : 0); j < N - 1; ++j) {
+      const long long msk = -(long long)((G >> j) & 1u);
+      const longlong2* col = D + (size_t)(2 * j) * N;
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        Yr[i] += col[i].x & msk;
+        Yi[i] += col[i].y & msk;
+      }
+    }
+
+    double br = 0.0, bi = 0.0;
+    for (uint32_t t = 0; t < nsteps; ++t) {
+      const int j = __ffs(t) - 1;
+      const uint32_t sb = ((t | kb) >> (j + 1)) & 1u;
+      const longlong2* col = t ? D + (size_t)(2 * j + sb) * N : zero;
+      CProd pa, pb;
+      cprod_init(pa);
+      cprod_init(pb);
+      int sa = 0, sbb = 0;
+#pragma unroll
+      for (int i = 0; i < N; i += 2) {
+        const longlong2 d0 = col[i];
+        Yr[i] += d0.x;
+        Yi[i] += d0.y;
+        sa += cprod_mul(pa, Yr[i], Yi[i]);
+        if (i + 1 < N) {
+          const longlong2 d1 = col[i + 1];
+          Yr[i + 1] += d1.x;
+          Yi[i + 1] += d1.y;
+          sbb += cprod_mul(pb, Yr[i + 1], Yi[i + 1]);
+        }
+      }
+      // merge chain b into chain a: b = (pb.r1 2^31 + pb.r0, ...) < 2^61 per part
+      const long long br_ = ((long long)pb.r1 << 31) | pb.r0;
+      const long long bi_ = ((long long)pb.i1 << 31) | pb.i0;
+      const int sm = cprod_mul(pa, br_, bi_);
+      const long long zr = ((long long)pa.r1 << 31) | pa.r0;
+      const long long zi = ((long long)pa.i1 << 31) | pa.i0;
+      const int e = ebase - (sa + sbb + sm);
+      double dr = ldexp((double)zr, e), di = ldexp((double)zi, e);
+      if ((t ^ gpar) & 1u) {
+        dr = -dr;
+        di = -di;
+      }
+      if (t - tlo < tcnt) {
+        br += dr;
+        bi += di;
+      }
+      if ((t & 7u) == 7u) {
+        accr = dd_add_d(accr, br);
+        acci = dd_add_d(acci, bi);
+        br = 0.0;
+        bi = 0.0;
+      }
+    }
+    accr = dd_add_d(accr, br);
+    acci = dd_add_d(acci, bi);
+  }
+
+  dd blkr = dd_block_sum(accr);
+  dd blki = dd_block_sum(acci);
+  dd* part = static_cast<dd*>(a.part);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = blkr;
+    part[2 * blockIdx.x + 1] = blki;
+  }
+  if (!arrive_last(a.counter)) return;
+  if (threadIdx.x < 32) {
+    dd tr = {0.0, 0.0}, ti = {0.0, 0.0};
+    for (unsigned int b = threadIdx.x; b < gridDim.x; b += 32) {
+      tr = dd_add(tr, part[2 * b]);
+      ti = dd_add(ti, part[2 * b + 1]);
+    }
+    tr = dd_warp_sum(tr);
+    ti = dd_warp_sum(ti);
+    if (threadIdx.x == 0) {
+      double* out = static_cast<double*>(a.out);
+      int32_t st = PERM_OK;
+      if (sh.nonfinite) st = PERM_EINVAL;
+      else if (sh.bound_log2 + N > 1000) st = PERM_ERANGE;
+      const double nan = __longlong_as_double(0x7ff8000000000000ll);
+      if (a.mode == 0) {
+        const double f = (N & 1) ? 2.0 : -2.0;
+        out[0] = st != PERM_OK ? nan : (sh.zero_row ? 0.0 : (tr.hi + tr.lo) * f);
+        out[1] = st != PERM_OK ? nan : (sh.zero_row ? 0.0 : (ti.hi + ti.lo) * f);
+      } else {
+        out[0] = st != PERM_OK ? nan : tr.hi;
+        out[1] = st != PERM_OK ? 0.0 : tr.lo;
+        out[2] = st != PERM_OK ? nan : ti.hi;
+        out[3] = st != PERM_OK ? 0.0 : ti.lo;
+      }
+      if (a.status) *a.status = st;
+      *a.counter = 0u;
+    }
+  }
+}
+
+}  // namespace permgpu

@@ -1,0 +1,21 @@
+// Instantiation tables of the dense kernels: one translation unit per range of
+// n so that the 63 compile-time sizes build in parallel.
+#pragma once
+#include <stddef.h>
+
+namespace permgpu {
+
+struct KernelEntry {
+  const void* fn;  // __global__ function
+  size_t smem;     // dynamic shared memory in bytes
+};
+
+KernelEntry real_entry_lo(int n);   // n = 1..24
+KernelEntry real_entry_mid(int n);  // n = 25..44
+KernelEntry real_entry_hi(int n);   // n = 45..63
+KernelEntry bin_lo_entry(int n);    // n = 1..32
+KernelEntry bin_hi_entry(int n);    // n = 33..63
+KernelEntry cplx_lo_entry(int n);   // n = 1..24
+KernelEntry cplx_hi_entry(int n);   // n = 25..63
+
+}  // namespace permgpu

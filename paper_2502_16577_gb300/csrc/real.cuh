@@ -1,0 +1,302 @@
+// Dense real Ryser kernel (Alg. 1 in Nijenhuis-Wilf form, chunked as Alg. 3
+// with the power-of-two chunks of Sec. 3.1.1), GB300-first:
+//
+//  * FP64 issues at 1/64 of the FP32 rate on this part, so the hot loop runs
+//    on the integer pipes.  Every row of A is scaled by a power of two and
+//    rounded once to 64-bit fixed point; the doubled row vector x' = 2x is then
+//    an exact int64 per row (Y_i), updated by one int64 add per row and step
+//    (no drift, unlike a binary64 running sum).
+//  * Column n-1 is rounded to odd multiples and the other columns to even ones,
+//    so Y_i is always odd and |Y_i| is (Y_i xor sign) | 1 - three integer ops.
+//  * prod_i x_i carries a 62..63-bit mantissa in two 32-bit halves and a
+//    power-of-two count: three 32x32->64 multiply-adds and one renormalising
+//    shift per factor (relative error below 2^-60 per factor).
+//  * Each step's signed term is rounded once to binary64 (built from the
+//    integer mantissa and exponent without the FP64 pipe), summed over 8
+//    steps in binary64 and carried into a per-lane double-double (Sec. 5).
+//  * The matrix is staged in shared memory as signed column increments
+//    (+D_j and -D_j, j < n-1), column-contiguous; all lanes of a warp flip the
+//    same column at the same step (aligned chunks, Sec. 3.1.1), so every
+//    column read is a shared-memory broadcast.
+//  * Lane partials are reduced warp -> CTA -> grid in a fixed order, so the
+//    result is bitwise reproducible for a given n and launch shape.
+#pragma once
+
+#include "common.cuh"
+
+namespace permgpu {
+
+// Running product: mantissa M = (m1:m0) in [2^62, 2^63) (up to the initial
+// value 2^62).  The renormalising shifts are accounted for by the caller.
+struct Prod {
+  uint32_t m0, m1;
+};
+
+__device__ __forceinline__ void prod_init(Prod& p) {
+  p.m0 = 0u;
+  p.m1 = 1u << 30;  // 2^62
+}
+
+// p <- p * A for A = a1:a0 < 2^63: v = floor(M A / 2^64) up to one unit (the
+// partial product m0*a0 is dropped and +1 unit is added back on average),
+// then M <- v << (30 - pos) with pos the index of the top set bit of v_hi, so
+// that M is back in [2^62, 2^63).  Returns pos (-1 if v_hi is zero, when the
+// shift is 31).  The multiply-adds issue on the IMAD pipe and the shifts on the
+// ALU pipe; the high limb of v comes from a carry-chained pair instead of a
+// zero-extended 64-bit addend.  Intermediates stay below 2^64 because
+// m1 < 2^31 and a1 < 2^31.
+__device__ __forceinline__ uint32_t prod_mul(Prod& p, uint32_t a0, uint32_t a1) {
+  uint32_t pos;
+  asm("{\n\t"
+      ".reg .u64 t, u;\n\t"
+      ".reg .u32 ul, uh, vl, vh, s;\n\t"
+      "mad.wide.u32 t, %2, %3, 4294967296;\n\t"
+      "mad.wide.u32 u, %1, %4, t;\n\t"
+      "mov.b64 {ul, uh}, u;\n\t"
+      "mad.lo.cc.u32 vl, %2, %4, uh;\n\t"
+      "madc.hi.u32 vh, %2, %4, 0;\n\t"
+      "bfind.u32 %0, vh;\n\t"
+      "sub.u32 s, 30, %0;\n\t"
+      "shf.l.wrap.b32 %2, vl, vh, s;\n\t"
+      "shl.b32 %1, vl, s;\n\t"
+      "}"
+      : "=r"(pos), "+r"(p.m0), "+r"(p.m1)
+      : "r"(a0), "r"(a1));
+  return pos;
+}
+
+// |Y| of an odd fixed-point row value Y (|Y| < 2^62) as (a0, a1), and the sign
+// mask m (0 or all ones).
+__device__ __forceinline__ void row_abs(unsigned long long Y, uint32_t& a0, uint32_t& a1, uint32_t& m) {
+  uint32_t ylo = (uint32_t)Y;
+  uint32_t yhi = (uint32_t)(Y >> 32);
+  m = (uint32_t)((int32_t)yhi >> 31);
+  a0 = (ylo ^ m) | 1u;
+  a1 = yhi ^ m;
+}
+
+// Y += d (two's complement), as a 64-bit multiply-add by one (a register the
+// compiler cannot fold) plus a 32-bit one on the high half, so that the row
+// update runs on the IMAD pipe next to the ALU-heavy normalisation.
+__device__ __forceinline__ void row_add(unsigned long long& Y, long long d, uint32_t one) {
+  uint32_t dlo = (uint32_t)(unsigned long long)d;
+  uint32_t dhi = (uint32_t)((unsigned long long)d >> 32);
+  asm("{\n\t"
+      ".reg .u32 lo, hi;\n\t"
+      "mad.wide.u32 %0, %1, %3, %0;\n\t"
+      "mov.b64 {lo, hi}, %0;\n\t"
+      "mad.lo.u32 hi, %2, %3, hi;\n\t"
+      "mov.b64 %0, {lo, hi};\n\t"
+      "}"
+      : "+l"(Y)
+      : "r"(dlo), "r"(dhi), "r"(one));
+}
+
+// Binary64 bit pattern of sign * M * 2^(f+1-1023-62) with M in [2^62, 2^63):
+// round to 53 bits, place the implicit bit on the exponent field (f is the
+// biased exponent minus one, clamped at 0 by the caller).
+__device__ __forceinline__ double prod_to_double(const Prod& p, uint32_t f, uint32_t signbit) {
+  uint32_t rlo, rhi;
+  asm("add.cc.u32 %0, %2, 512;\n\t"
+      "addc.u32 %1, %3, 0;"
+      : "=r"(rlo), "=r"(rhi)
+      : "r"(p.m0), "r"(p.m1));
+  uint32_t lo32 = __funnelshift_r(rlo, rhi, 10);
+  uint32_t hi32 = (rhi >> 10) + (f << 20) + signbit;
+  return __hiloint2double((int)hi32, (int)lo32);
+}
+
+// Shared-memory layout (dynamic): Dpm[(2j + s) * NP + i] for j < n-1,
+// s = 0 (+D_ij, the column enters) or 1 (-D_ij, it leaves); then base[NP]
+// (Y at g = 0), then NP zeros (the "update" of a chunk's first step).
+template <int N>
+struct RealLayout {
+  static constexpr int NP = (N + 1) & ~1;  // rows padded to even: 16-byte pairs
+  static constexpr int NCOL = N > 1 ? N - 1 : 0;
+  static constexpr size_t kD = 0;
+  static constexpr size_t kBase = kD + sizeof(long long) * 2 * NCOL * NP;
+  static constexpr size_t kZero = kBase + sizeof(long long) * NP;  // NP zeros
+  static constexpr size_t kBytes = kZero + sizeof(long long) * NP;
+};
+
+struct RealShared {
+  int sum_s;       // sum of the row scale exponents s_i
+  int bound_log2;  // sum of k_i - 1, k_i = binary exponent of row i's absolute sum
+  int nonfinite;
+  int zero_row;
+};
+
+// Stage A into shared memory as fixed-point column increments.
+//   s_i = 61 - k_i with sum_j |a_ij| in [2^(k_i - 1), 2^k_i);
+//   Q_ij = 2 round(a_ij 2^(s_i - 1)) for j < n-1 (even),
+//   Q_{i,n-1} = 2 floor(a 2^(s_i - 1)) + 1 (odd);
+//   Y_i(g) = sum_j delta_j Q_ij  (delta_j = +1 if column j is in the subset
+//   or j = n-1, else -1)  represents x'_i = 2 x_i scaled by 2^s_i, and
+//   |Y_i| <= sum_j |Q_ij| < 2^61 + n.
+template <int N>
+__device__ __forceinline__ void real_stage(const double* __restrict__ A, unsigned char* smem, RealShared& sh) {
+  using L = RealLayout<N>;
+  long long* D = reinterpret_cast<long long*>(smem + L::kD);
+  long long* base = reinterpret_cast<long long*>(smem + L::kBase);
+  long long* zero = reinterpret_cast<long long*>(smem + L::kZero);
+  if (threadIdx.x == 0) {
+    sh.sum_s = 0;
+    sh.bound_log2 = 0;
+    sh.nonfinite = 0;
+    sh.zero_row = 0;
+  }
+  __syncthreads();
+  int i = threadIdx.x;
+  if (i < N) {
+    const double* row = A + (size_t)i * N;
+    double absum = 0.0;
+    int fin = 1;
+    for (int j = 0; j < N; ++j) {
+      double a = row[j];
+      fin &= isfinite(a) ? 1 : 0;
+      absum += fabs(a);
+    }
+    int k = 0;
+    if (fin && absum > 0.0) frexp(absum, &k);
+    int s = 61 - k;
+    long long qsum = 0;
+    for (int j = 0; j < N - 1; ++j) {
+      long long q = fin ? __double2ll_rn(ldexp(row[j], s - 1)) : 0;
+      long long Q = 2 * q;
+      qsum += Q;
+      D[(2 * j) * L::NP + i] = 2 * Q;
+      D[(2 * j + 1) * L::NP + i] = -2 * Q;
+    }
+    long long qn = fin ? 2 * __double2ll_rd(ldexp(row[N - 1], s - 1)) + 1 : 1;
+    base[i] = qn - qsum;
+    zero[i] = 0;
+    atomicAdd(&sh.sum_s, s);
+    atomicAdd(&sh.bound_log2, k - 1);
+    if (!fin) atomicOr(&sh.nonfinite, 1);
+    if (fin && absum == 0.0) atomicOr(&sh.zero_row, 1);
+  } else if (i < L::NP) {
+    for (int j = 0; j < N - 1; ++j) {
+      D[(2 * j) * L::NP + i] = 0;
+      D[(2 * j + 1) * L::NP + i] = 0;
+    }
+    base[i] = 1;
+    zero[i] = 0;
+  }
+  __syncthreads();
+}
+
+template <int N>
+__global__ void __launch_bounds__(kBlock, (N <= 48 ? 2 : 1)) ryser_real_kernel(RyserArgs a) {
+  using L = RealLayout<N>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ RealShared sh;
+  real_stage<N>(static_cast<const double*>(a.A), smem, sh);
+  const long long* D = reinterpret_cast<const long long*>(smem + L::kD);
+  const long long* base = reinterpret_cast<const long long*>(smem + L::kBase);
+  const long long* zero = reinterpret_cast<const long long*>(smem + L::kZero);
+
+  // exponent bookkeeping, see prod_to_double: the term is
+  // sign * M * 2^(64N + 3 - sum_s - sum_lz - 62) in units of prod_i x_i.
+  const int K1 = 64 * N + 1025 - sh.sum_s;
+  const uint32_t one = (uint32_t)a.one;  // 1, opaque to the compiler
+  const bool bad = sh.nonfinite || sh.bound_log2 + N > 1000;
+  const bool skip = bad || sh.zero_row;
+
+  dd acc = {0.0, 0.0};
+  const int lane = threadIdx.x & 31;
+  const uint64_t warp_id = (uint64_t)(blockIdx.x * kBlock + threadIdx.x) >> 5;
+  const uint64_t nwarps = (uint64_t)(gridDim.x * kBlock) >> 5;
+  const uint64_t ngroups = skip ? 0 : (a.nchunks + 31) / 32;
+  const uint32_t nsteps = 1u << a.c;
+
+  for (uint64_t q = warp_id; q < ngroups; q += nwarps) {
+    const uint64_t kk = q * 32 + lane;
+    const bool active = kk < a.nchunks;
+    const uint64_t k = a.k_begin + kk;
+    const uint64_t g0 = k << a.c;
+    uint32_t tlo, tcnt;
+    chunk_window(a, g0, active, tlo, tcnt);
+    const uint32_t kb = (uint32_t)(k & 1u) << a.c;  // bit c of g, for the chunk's middle step
+    const uint32_t gpar = (uint32_t)(g0 & 1u);      // parity of g0 (odd only when c = 0)
+
+    // Y at Gray(g0): base plus every column whose Gray bit is set.  Bits below
+    // c-1 of Gray(k 2^c) are zero.
+    unsigned long long Y[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) Y[i] = (unsigned long long)base[i];
+    const uint64_t G = gray64(g0);
+    for (int j = (a.c > 0 ? a.c - 1 : 0); j < N - 1; ++j) {
+      const long long msk = -(long long)((G >> j) & 1u);
+      const long long* col = D + (size_t)(2 * j) * L::NP;
+#pragma unroll
+      for (int i = 0; i < N; ++i) Y[i] += (unsigned long long)(col[i] & msk);
+    }
+
+    double bacc = 0.0;
+    for (uint32_t t = 0; t < nsteps; ++t) {
+      // column j = ctz(t) enters or leaves (Alg. 1: j = log2(Gray_t xor
+      // Gray_{t-1}), entering iff bit j+1 of g is clear); t = 0 is the chunk's
+      // start state and updates nothing (its column pointer reads zeros).
+      const int j = __ffs(t) - 1;
+      const uint32_t sb = ((t | kb) >> (j + 1)) & 1u;
+      const longlong2* col = reinterpret_cast<const longlong2*>(t ? D + (size_t)(2 * j + sb) * L::NP : zero);
+      Prod pa, pb;
+      prod_init(pa);
+      prod_init(pb);
+      uint32_t neg = 0, epos = 0;  // -(number of negative factors), sum of pos
+#pragma unroll
+      for (int p = 0; p < L::NP / 2; ++p) {
+        const longlong2 d = col[p];
+        uint32_t a0, a1, ma, b0, b1, mb = 0, qb = 0;
+        row_add(Y[2 * p], d.x, one);
+        row_abs(Y[2 * p], a0, a1, ma);
+        if (2 * p + 1 < N) {
+          row_add(Y[2 * p + 1], d.y, one);
+          row_abs(Y[2 * p + 1], b0, b1, mb);
+        }
+        const uint32_t qa = prod_mul(pa, a0, a1);
+        if (2 * p + 1 < N) qb = prod_mul(pb, b0, b1);
+        neg = neg + ma + mb;
+        epos = epos + qa + qb;
+      }
+      epos += prod_mul(pa, pb.m0, pb.m1);
+      // the N + 1 multiplies (N rows and the merge) shifted by sum(30 - pos)
+      const int shifts = 30 * (N + 1) - (int)epos;
+      const int f = K1 - shifts - (N + 1);
+      const uint32_t signbit = (neg ^ t ^ gpar) << 31;
+      const double term = prod_to_double(pa, (uint32_t)max(f, 0), signbit);
+      if (t - tlo < tcnt) bacc += term;
+      if ((t & 7u) == 7u) {
+        acc = dd_add_d(acc, bacc);
+        bacc = 0.0;
+      }
+    }
+    acc = dd_add_d(acc, bacc);
+  }
+
+  dd blk = dd_block_sum(acc);
+  dd* part = static_cast<dd*>(a.part);
+  if (threadIdx.x == 0) part[blockIdx.x] = blk;
+  if (!arrive_last(a.counter)) return;
+  if (threadIdx.x < 32) {
+    dd tot = dd_sum_partials(part, gridDim.x);
+    if (threadIdx.x == 0) {
+      double* out = static_cast<double*>(a.out);
+      int32_t st = PERM_OK;
+      if (sh.nonfinite) st = PERM_EINVAL;
+      else if (sh.bound_log2 + N > 1000) st = PERM_ERANGE;
+      if (a.mode == 0) {
+        const double f = (N & 1) ? 2.0 : -2.0;  // 4 (n mod 2) - 2
+        out[0] = st != PERM_OK ? __longlong_as_double(0x7ff8000000000000ll)
+                 : (sh.zero_row ? 0.0 : (tot.hi + tot.lo) * f);
+      } else {
+        out[0] = st != PERM_OK ? __longlong_as_double(0x7ff8000000000000ll) : tot.hi;
+        out[1] = st != PERM_OK ? 0.0 : tot.lo;
+      }
+      if (a.status) *a.status = st;
+      *a.counter = 0u;
+    }
+  }
+}
+
+}  // namespace permgpu
