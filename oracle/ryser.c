@@ -21,7 +21,7 @@
  *                                      the high-precision reference of Sec. 5's
  *                                      accuracy study.
  *   oracle_ryser_c128_range            Alg. 1 over complex entries (complex support is
- *                                      claimed in Secs. 1 and 6; same recurrence in C).
+ *                                      claimed in Secs. 1 and 7; same recurrence in C).
  *   oracle_spa_ryser_f64_range         Alg. 2 (SPARYSER): CRS for the row sums, CCS for
  *                                      the column updates.
  *   oracle_ryser_bin_plain             Eq. 2 (Ryser over all 2^n column subsets, no
