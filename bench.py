@@ -1,0 +1,385 @@
+#!/usr/bin/env python
+"""Benchmark of the Ryser / Nijenhuis-Wilf Gray-code sweep on GB300.
+
+One step = one pass of the whole hot path over the dense workload:
+  * dense real n=40, uniform [-1, 1)            (2^39 Gray steps)
+  * 0/1 Bernoulli(0.5) n=36, exact              (2^35 Gray steps)
+  * complex128 Haar-random 32 x 32 unitary      (2^31 Gray steps)
+The metric is Gray-code steps per second over all three (whole job, all
+ranks).  Under torchrun every permanent's Gray range is split evenly across
+ranks (perm_range per rank), the partials are gathered and rank 0 combines
+them (perm_combine): the single exchange of the method (Secs. 3.3, 6.3).
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle
+instead (as it stands, all host cores, a bounded sample of the same workload
+per step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synthetic as syn  # noqa: E402
+
+METRIC = "Gray-code steps/s & FP64-peak fraction (n=40 dense); batched perms/s; grad/fwd"
+WORKLOAD = "dense real n=40 U[-1,1) + 0/1 Bernoulli(0.5) n=36 + complex128 Haar 32x32 (one permanent each per step)"
+L2_FLUSH_BYTES = 256 << 20  # larger than the 129 MB L2
+
+
+def workloads():
+    return [
+        ("real40", syn.dense_real_40()),
+        ("bin36", syn.binary_36()),
+        ("cplx32", syn.complex_32()),
+    ]
+
+
+def steps_of(n: int) -> int:
+    return 1 << (n - 1)
+
+
+# ----------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]), "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
+
+
+# -------------------------------------------------------------- distributed
+
+def dist_setup(ngpus: int):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        backend = "nccl" if _cuda_ok() else "gloo"
+        dist.init_process_group(backend=backend)
+        return rank, world, local, dist
+    return 0, 1, 0, None
+
+
+def _cuda_ok() -> bool:
+    try:
+        import torch
+
+        return torch.cuda.is_available()
+    except ImportError:
+        return False
+
+
+def shard(n_steps: int, rank: int, world: int):
+    """Contiguous share of [0, n_steps) for one rank (Sec. 6.3: the iteration
+    space is first split per GPU)."""
+    base, rem = divmod(n_steps, world)
+    lo = rank * base + min(rank, rem)
+    return lo, lo + base + (1 if rank < rem else 0)
+
+
+# ---------------------------------------------------------------- CPU oracle
+
+def oracle_sample(frac_log2: int, threads: int):
+    """Time the oracle (as it stands) on a bounded sample of every permanent:
+    the first 2^(n-1-frac_log2) steps of each Gray range.  Returns
+    (steps, seconds)."""
+    import oracle
+
+    total, secs = 0, 0.0
+    for name, A in workloads():
+        n = A.shape[0]
+        s = max(1, steps_of(n) >> frac_log2)
+        fn = {"real40": oracle.ryser_f64_range, "bin36": oracle.ryser_bin_range,
+              "cplx32": oracle.ryser_c128_range}[name]
+        t0 = time.perf_counter()
+        fn(A, 0, s, threads=threads)
+        secs += time.perf_counter() - t0
+        total += s
+    return total, secs
+
+
+def run_reference(args):
+    # under torchrun only rank 0 runs the CPU oracle; the others exit at once
+    if int(os.environ.get("RANK", "0")) != 0:
+        return 0
+    threads = os.cpu_count() or 1
+    frac = 10  # 2^-10 of each Gray range per step
+    for _ in range(args.warmup):
+        oracle_sample(frac, threads)
+    tot_steps, tot_secs = 0, 0.0
+    for _ in range(args.steps):
+        s, t = oracle_sample(frac, threads)
+        tot_steps += s
+        tot_secs += t
+    value = tot_steps / tot_secs
+    sample = f"first 2^-{frac} of each Gray range per step (real40 2^29, bin36 2^25, cplx32 2^21 steps)"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_secs / args.steps,
+        "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "oracle": "CPU Ryser/N-W (Alg. 1/3), pthreads"},
+        "cpu_baseline": {"value": value, "unit": "steps/s", "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------- GPU arm
+
+def profiled_traffic(kernel_file: str, summary: str):
+    """DRAM bytes per launch recorded in a committed ncu summary, if the kernel
+    source it was taken from is unchanged (the summary carries its hash)."""
+    import hashlib
+
+    try:
+        text = open(os.path.join(ROOT, "profiles", summary)).read()
+        src = open(os.path.join(ROOT, "paper_2502_16577_gb300", "csrc", kernel_file), "rb").read()
+    except OSError:
+        return None
+    digest = hashlib.sha256(src).hexdigest()[:16]
+    traffic, tag = None, None
+    for line in text.splitlines():
+        if line.startswith("dram_bytes_per_launch:"):
+            traffic = float(line.split(":", 1)[1])
+        if line.startswith("source_sha256_16:"):
+            tag = line.split(":", 1)[1].strip()
+    return traffic if tag == digest else None
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def run_gpu(args):
+    import torch
+
+    import paper_2502_16577_gb300 as pg
+
+    rank, world, local, dist = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg.load()
+    stream = torch.cuda.current_stream(dev)
+    mats = []
+    for name, A in workloads():
+        t = torch.from_numpy(np.ascontiguousarray(A)).to(dev)
+        n = A.shape[0]
+        lo, hi = shard(steps_of(n), rank, world)
+        typ = pg.perm_type_of(t.dtype)
+        words = {pg.PERM_F64: 2, pg.PERM_C128: 4, pg.PERM_BIN: 3}[typ]
+        out = torch.zeros(words, dtype=torch.int64 if typ == pg.PERM_BIN else torch.float64, device=dev)
+        mats.append(dict(name=name, A=t, host=A, n=n, lo=lo, hi=hi, type=typ, out=out,
+                         status=torch.zeros(1, dtype=torch.int32, device=dev)))
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def one_step(real_events=None):
+        for m in mats:
+            if m["name"] == "real40" and real_events is not None:
+                real_events[0].record(stream)
+            if world == 1:
+                pg.perm_async(m["A"], m["out"], m["status"], stream)
+            else:
+                pg.perm_range_async(m["A"], m["lo"], m["hi"], m["out"], m["status"], stream)
+            if m["name"] == "real40" and real_events is not None:
+                real_events[1].record(stream)
+
+    def gather_and_combine():
+        """The exchange: every rank's partials to rank 0, combined on the host."""
+        results = {}
+        for m in mats:
+            if world == 1:
+                results[m["name"]] = m["out"].cpu().numpy().copy()
+                continue
+            parts = [torch.zeros_like(m["out"]) for _ in range(world)]
+            dist.all_gather(parts, m["out"])
+            if rank == 0:
+                vals = [p.cpu().numpy() for p in parts]
+                if m["type"] == pg.PERM_BIN:
+                    vals = [sum(int(w) % (1 << 64) << (64 * i) for i, w in enumerate(v)) for v in vals]
+                results[m["name"]] = pg.perm_combine(m["type"], m["n"], vals)
+        return results
+
+    # warm-up (untimed)
+    for _ in range(args.warmup):
+        one_step()
+        torch.cuda.synchronize(dev)
+        gather_and_combine()
+    for m in mats:
+        st = int(m["status"].item())
+        if st not in (0,):
+            raise RuntimeError(f"{m['name']}: status {st}")
+
+    peaks = pg.pipe_peaks(stream) if rank == 0 else {}
+
+    sampler = ClockSampler(local)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    sampler.start()
+    step_ms, real_ms = [], []
+    for _ in range(args.steps):
+        flush.zero_()  # L2 flush between timed steps (outside the events)
+        e0, e1, r0, r1 = ev(), ev(), ev(), ev()
+        e0.record(stream)
+        one_step((r0, r1))
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        gather_and_combine()
+        step_ms.append(e0.elapsed_time(e1))
+        real_ms.append(r0.elapsed_time(r1))
+    torch.cuda.synchronize(dev)
+    if dist is not None:
+        dist.barrier()
+    clocks = sampler.stop()
+    local_ms = sum(step_ms)
+    if dist is not None:
+        t = torch.tensor([local_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        local_ms = float(t.item())
+    total_steps = sum(steps_of(m["n"]) for m in mats)
+    value = total_steps * args.steps / (local_ms * 1e-3)
+
+    # end to end through the public host-buffer entry point (rank 0 of N=1 only,
+    # or every rank on its shard through the device path plus copies)
+    e2e = None
+    if world == 1:
+        host = [(m["host"], m["n"]) for m in mats]
+        h2d = sum(a.nbytes for a, _ in host)
+        d2h = 8 + 16 + 16
+        ke = max(1, min(args.steps, 2))
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            for a, _ in host:
+                pg.perm_host(a)
+        dt = time.perf_counter() - t0
+        e2e = {"value": total_steps * ke / dt, "unit": "steps/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+
+    if rank != 0:
+        return 0
+
+    # roofline of the dominant kernel (dense real n=40): issue-slot work of the
+    # integer factor sequence against the SM issue peak; FP64 view alongside
+    n40 = 40
+    per_step_slots = 14 * n40 + 10
+    real_s = statistics.mean(real_ms) * 1e-3
+    real_steps = mats[0]["hi"] - mats[0]["lo"]
+    mp = measured_peaks()
+    sm_max = float(mp.get("sm_max_mhz", 2070.0))
+    import torch as _t
+
+    nsm = _t.cuda.get_device_properties(dev).multi_processor_count
+    issue_peak = nsm * 128 * sm_max * 1e6  # lane-instructions/s
+    achieved = per_step_slots * real_steps / real_s
+    fp64_peak = peaks.get("fp64_fma", 0.0)  # FP64 instructions/s (an FMA counts once)
+    fp64_equiv = 2 * n40 * real_steps / real_s
+    line = {
+        "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": local_ms / args.steps, "higher_is_better": True,
+        "scaling": "strong", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "l2": "flushed between timed steps (256 MiB write, outside the events)",
+                   "steps_per_pass": total_steps, "split": "Gray range split evenly across ranks" if world > 1
+                   else "one launch per permanent", "arith": "int64 fixed-point rows, 62-bit integer products, "
+                   "binary64 + double-double sums; 0/1 exact mod 2^192"},
+        "gpu_launches": 3 * args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": issue_peak / 1e12,
+                     "unit": "Tinst/s", "frac": achieved / issue_peak,
+                     "traffic": args.traffic if args.traffic is not None else
+                     profiled_traffic("real.cuh", "ryser_real_kernel_n40.md"),
+                     "kernel": "ryser_real_kernel<40>", "work_per_step": per_step_slots,
+                     "peak_from": f"{nsm} SMs x 128 issue lanes x {sm_max:.0f} MHz (max SM clock)"},
+        "fp64_view": {"steps_per_s": real_steps / real_s, "fp64_equiv_ops_per_s": fp64_equiv,
+                      "fp64_pipe_peak_ops_per_s": fp64_peak,
+                      "frac_of_fp64_peak": fp64_equiv / fp64_peak if fp64_peak else None,
+                      "paper_gv100_steps_per_s": 2 ** 39 / 14.17},
+        "pipe_peaks": peaks,
+        "per_config_ms": {"real40": statistics.mean(real_ms)},
+        "clocks": clocks,
+        "e2e": e2e,
+    }
+    if not args.no_cpu_baseline:
+        s, t = oracle_sample(8, os.cpu_count() or 1)
+        line["cpu_baseline"] = {"value": s / t, "unit": "steps/s", "cores": os.cpu_count() or 1, "kind": "oracle",
+                                "sample": "first 2^-8 of each Gray range (real40 2^31, bin36 2^27, cplx32 2^23 steps)",
+                                "seconds": t}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="DRAM bytes per launch of the dominant kernel from an ncu capture")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -123,6 +123,18 @@ int perm_combine(int type, int n, const void* partials, int count, void* out);
  */
 int perm_host(const void* A_host, int n, int type, void* out_host, void* stream);
 
+/*
+ * perm_pipe_peaks - measured throughput of the pipes the kernels use, the
+ * denominators of the benchmark's roofline fractions (measurement
+ * infrastructure; the paper has no counterpart).  Runs microbenchmarks on the
+ * current device (8 independent chains of one instruction per thread, 4 CTAs
+ * of 256 threads per SM, best of 3) and writes lane-instructions per second:
+ *   out[0] fma.rn.f64, out[1] add.rn.f64, out[2] mad.lo.u32,
+ *   out[3] mad.wide.u32, out[4] shf.l.wrap.b32  (first count entries).
+ *   out  host double[count], 1 <= count <= 5.  Waits for the stream.
+ */
+int perm_pipe_peaks(double* out, int count, void* stream);
+
 /* Human-readable name of a perm_status_t; never NULL. */
 const char* perm_status_string(int status);
 

@@ -21,7 +21,7 @@ import numpy as np
 from . import _lib
 from ._lib import PERM_BIN, PERM_C128, PERM_F64, PermError, check, load
 
-__all__ = ["perm", "perm_async", "perm_range", "perm_combine", "perm_host", "perm_type_of", "PermError",
+__all__ = ["perm", "perm_async", "perm_range", "perm_range_async", "perm_combine", "perm_host", "pipe_peaks", "perm_type_of", "PermError",
            "PERM_F64", "PERM_C128", "PERM_BIN", "load"]
 
 
@@ -106,6 +106,19 @@ def perm(A, stream=None):
     return _u(o)
 
 
+def perm_range_async(A, g_begin: int, g_end: int, out, status=None, stream=None) -> None:
+    """Enqueue perm_range on a stream without waiting (out: float64[2] real,
+    float64[4] complex, int64[3] for 0/1; status: int32[1])."""
+    lib = load()
+    A = _as_device_matrix(A)
+    t = perm_type_of(A.dtype)
+    h, _ = _stream_handle(stream)
+    rc = lib.perm_range(ctypes.c_void_p(A.data_ptr()), A.shape[0], t, int(g_begin), int(g_end),
+                        ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(status.data_ptr() if status is not None else 0),
+                        h)
+    check(rc, "perm_range")
+
+
 def perm_range(A, g_begin: int, g_end: int, stream=None):
     """Raw partial over steps [g_begin, g_end): (hi, lo) for float64,
     (re_hi, re_lo, im_hi, im_lo) for complex128, an int mod 2^192 for 0/1."""
@@ -150,6 +163,19 @@ def perm_combine(t: int, n: int, partials):
     if t == PERM_C128:
         return complex(float(out[0]), float(out[1]))
     return _u(out)
+
+
+PIPE_NAMES = ("fp64_fma", "fp64_add", "imad", "imad_wide", "shf")
+
+
+def pipe_peaks(stream=None) -> dict:
+    """Measured lane-instructions per second of the pipes the kernels use
+    (perm_pipe_peaks)."""
+    lib = load()
+    out = (ctypes.c_double * len(PIPE_NAMES))()
+    h, _ = _stream_handle(stream)
+    check(lib.perm_pipe_peaks(out, len(PIPE_NAMES), h), "perm_pipe_peaks")
+    return dict(zip(PIPE_NAMES, list(out)))
 
 
 def perm_host(A, stream=None):

@@ -17,7 +17,8 @@ _vp = ctypes.c_void_p
 _i32p = ctypes.POINTER(ctypes.c_int32)
 _lib = None
 
-SYMBOLS = ("perm", "perm_range", "perm_combine", "perm_host", "perm_status_string", "perm_abi_version")
+SYMBOLS = ("perm", "perm_range", "perm_combine", "perm_host", "perm_pipe_peaks", "perm_status_string",
+           "perm_abi_version")
 
 
 class PermError(RuntimeError):
@@ -49,6 +50,8 @@ def load(build_if_missing: bool = False):
     lib.perm_combine.argtypes = [ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, _vp]
     lib.perm_host.restype = ctypes.c_int
     lib.perm_host.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp]
+    lib.perm_pipe_peaks.restype = ctypes.c_int
+    lib.perm_pipe_peaks.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.c_int, _vp]
     lib.perm_status_string.restype = ctypes.c_char_p
     lib.perm_status_string.argtypes = [ctypes.c_int]
     lib.perm_abi_version.restype = ctypes.c_int
