@@ -117,6 +117,21 @@ int perm_range(const void* A, int n, int type, uint64_t g_begin, uint64_t g_end,
 int perm_combine(int type, int n, const void* partials, int count, void* out);
 
 /*
+ * perm_sparse - permanent of an n x n real matrix given in compressed column
+ * storage (Fig. 1): column j holds rows rids[cptrs[j] .. cptrs[j+1]-1]
+ * (strictly increasing) with values cvals[...]; cptrs[0] = 0, cptrs[n] = nnz.
+ * Alg. 2: each step updates only the nonzeros of the changed column, and the
+ * product is skipped while some x_i is exactly zero (such a term is zero).
+ *
+ *   cptrs, rids, cvals  device; int32_t[n+1], int32_t[nnz], double[nnz].
+ *   out                 device double[1];  status as for perm().
+ * The CCS structure is checked on the device: a malformed one gives
+ * PERM_EINVAL in *status and NaN in out.
+ */
+int perm_sparse(int n, const int32_t* cptrs, const int32_t* rids, const double* cvals, int64_t nnz,
+                double* out, int32_t* status, void* stream);
+
+/*
  * perm_host - perm() on host buffers: copies A in, runs perm() on stream,
  * copies the result out and waits.  Returns the device status as well.
  *   A_host   host, layout as perm()'s A;  out_host  host, layout as perm()'s out.

@@ -21,7 +21,7 @@ import numpy as np
 from . import _lib
 from ._lib import PERM_BIN, PERM_C128, PERM_F64, PermError, check, load
 
-__all__ = ["perm", "perm_async", "perm_range", "perm_range_async", "perm_combine", "perm_host", "pipe_peaks", "perm_type_of", "PermError",
+__all__ = ["perm", "perm_async", "perm_range", "perm_range_async", "perm_combine", "perm_sparse", "perm_sparse_async", "perm_host", "pipe_peaks", "perm_type_of", "PermError",
            "PERM_F64", "PERM_C128", "PERM_BIN", "load"]
 
 
@@ -163,6 +163,34 @@ def perm_combine(t: int, n: int, partials):
     if t == PERM_C128:
         return complex(float(out[0]), float(out[1]))
     return _u(out)
+
+
+def perm_sparse_async(n: int, cptrs, rids, cvals, out, status=None, stream=None) -> None:
+    """Enqueue the permanent of an n x n CCS matrix (device int32 cptrs[n+1],
+    int32 rids[nnz], float64 cvals[nnz]) into out (float64[1])."""
+    lib = load()
+    torch = _torch()
+    for t, dt in ((cptrs, torch.int32), (rids, torch.int32), (cvals, torch.float64)):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != dt or not t.is_contiguous():
+            raise TypeError("CCS arrays must be contiguous CUDA tensors (int32, int32, float64)")
+    h, _ = _stream_handle(stream)
+    rc = lib.perm_sparse(int(n), ctypes.c_void_p(cptrs.data_ptr()), ctypes.c_void_p(rids.data_ptr()),
+                         ctypes.c_void_p(cvals.data_ptr()), int(rids.numel()), ctypes.c_void_p(out.data_ptr()),
+                         ctypes.c_void_p(status.data_ptr() if status is not None else 0), h)
+    check(rc, "perm_sparse")
+
+
+def perm_sparse(n: int, cptrs, rids, cvals, stream=None) -> float:
+    """Permanent of an n x n real matrix in CCS form (Alg. 2); waits for it."""
+    torch = _torch()
+    dev = cptrs.device
+    out = torch.zeros(1, dtype=torch.float64, device=dev)
+    status = torch.full((1,), -1, dtype=torch.int32, device=dev)
+    perm_sparse_async(n, cptrs, rids, cvals, out, status, stream)
+    _, s = _stream_handle(stream)
+    s.synchronize()
+    check(int(status.item()), "perm_sparse")
+    return float(out.item())
 
 
 PIPE_NAMES = ("fp64_fma", "fp64_add", "imad", "imad_wide", "shf")

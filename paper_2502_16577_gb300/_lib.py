@@ -17,8 +17,8 @@ _vp = ctypes.c_void_p
 _i32p = ctypes.POINTER(ctypes.c_int32)
 _lib = None
 
-SYMBOLS = ("perm", "perm_range", "perm_combine", "perm_host", "perm_pipe_peaks", "perm_status_string",
-           "perm_abi_version")
+SYMBOLS = ("perm", "perm_range", "perm_combine", "perm_sparse", "perm_host", "perm_pipe_peaks",
+           "perm_status_string", "perm_abi_version")
 
 
 class PermError(RuntimeError):
@@ -48,6 +48,8 @@ def load(build_if_missing: bool = False):
     lib.perm_range.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, _vp, _vp, _vp]
     lib.perm_combine.restype = ctypes.c_int
     lib.perm_combine.argtypes = [ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, _vp]
+    lib.perm_sparse.restype = ctypes.c_int
+    lib.perm_sparse.argtypes = [ctypes.c_int, _vp, _vp, _vp, ctypes.c_int64, _vp, _vp, _vp]
     lib.perm_host.restype = ctypes.c_int
     lib.perm_host.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp]
     lib.perm_pipe_peaks.restype = ctypes.c_int

@@ -46,6 +46,16 @@ __device__ __forceinline__ dd dd_add_d(dd a, double b) {
   return dd_make(s, e);
 }
 
+// acc += hi + lo with an exact TwoSum of the heads (Knuth) and the tails and
+// the head's rounding error carried in acc.lo.
+__device__ __forceinline__ void dd_acc(dd& acc, double hi, double lo) {
+  const double s = acc.hi + hi;
+  const double bv = s - acc.hi;
+  const double err = (acc.hi - (s - bv)) + (hi - bv);
+  acc.hi = s;
+  acc.lo += err + lo;
+}
+
 __device__ __forceinline__ dd dd_shfl_down(dd v, int off) {
   dd r;
   r.hi = __shfl_down_sync(0xffffffffu, v.hi, off);

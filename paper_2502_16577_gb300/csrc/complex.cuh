@@ -9,9 +9,10 @@
 // that every partial product is a signed 32x32->64 multiply-add with no sign
 // handling:  (p1 2^31 + p0)(y1 2^31 + y0) = p1 y1 2^62 + (p1 y0 + p0 y1) 2^31 + ...
 // After each complex multiply the pair is renormalised so that the larger part
-// has its top bit at 2^60.  Terms are rounded once to binary64 (the
-// conversion runs on the otherwise idle FP64 pipe), summed over 8 steps and
-// carried into double-double lane partials (Sec. 5).
+// has its top bit at 2^60.  Each part of a term is split exactly into a
+// binary64 head and tail (the conversions run on the otherwise idle FP64
+// pipe) and added to double-double lane partials with an exact TwoSum
+// (Sec. 5).
 #pragma once
 
 #include "common.cuh"
@@ -174,7 +175,6 @@ __global__ void __launch_bounds__(kBlock, (N <= 8 ? 2 : 1)) ryser_cplx_kernel(Ry
       }
     }
 
-    double br = 0.0, bi = 0.0;
     for (uint32_t t = 0; t < nsteps; ++t) {
       const int j = __ffs(t) - 1;
       const uint32_t sb = ((t | kb) >> (j + 1)) & 1u;
@@ -203,24 +203,17 @@ __global__ void __launch_bounds__(kBlock, (N <= 8 ? 2 : 1)) ryser_cplx_kernel(Ry
       const long long zr = ((long long)pa.r1 << 31) | pa.r0;
       const long long zi = ((long long)pa.i1 << 31) | pa.i0;
       const int e = ebase - (sa + sbb + sm);
-      double dr = ldexp((double)zr, e), di = ldexp((double)zi, e);
-      if ((t ^ gpar) & 1u) {
-        dr = -dr;
-        di = -di;
-      }
-      if (t - tlo < tcnt) {
-        br += dr;
-        bi += di;
-      }
-      if ((t & 7u) == 7u) {
-        accr = dd_add_d(accr, br);
-        acci = dd_add_d(acci, bi);
-        br = 0.0;
-        bi = 0.0;
-      }
+      // each part as an exact head + tail pair: head = round(z), tail = z - head
+      // (|tail| <= 2^8), both scaled by 2^e (powers of two: exact)
+      const double hr = (double)zr, hi_ = (double)zi;
+      const double lr = (double)(zr - __double2ll_rn(hr)), li = (double)(zi - __double2ll_rn(hi_));
+      const double sc = ldexp(((t ^ gpar) & 1u) ? -1.0 : 1.0, e);
+      const bool in = t - tlo < tcnt;
+      dd_acc(accr, in ? hr * sc : 0.0, in ? lr * sc : 0.0);
+      dd_acc(acci, in ? hi_ * sc : 0.0, in ? li * sc : 0.0);
     }
-    accr = dd_add_d(accr, br);
-    acci = dd_add_d(acci, bi);
+    accr = dd_make(accr.hi, accr.lo);
+    acci = dd_make(acci.hi, acci.lo);
   }
 
   dd blkr = dd_block_sum(accr);

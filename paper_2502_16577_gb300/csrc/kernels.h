@@ -2,6 +2,7 @@
 // n so that the 63 compile-time sizes build in parallel.
 #pragma once
 #include <stddef.h>
+#include <stdint.h>
 
 namespace permgpu {
 
@@ -17,5 +18,8 @@ KernelEntry bin_lo_entry(int n);    // n = 1..32
 KernelEntry bin_hi_entry(int n);    // n = 33..63
 KernelEntry cplx_lo_entry(int n);   // n = 1..24
 KernelEntry cplx_hi_entry(int n);   // n = 25..63
+
+// Chunk exponent of a launch over nsteps Gray steps (api.cu).
+int plan_chunk_exponent(int n, uint64_t nsteps, int warps_resident);
 
 }  // namespace permgpu

@@ -11,9 +11,11 @@
 //  * prod_i x_i carries a 62..63-bit mantissa in two 32-bit halves and a
 //    power-of-two count: three 32x32->64 multiply-adds and one renormalising
 //    shift per factor (relative error below 2^-60 per factor).
-//  * Each step's signed term is rounded once to binary64 (built from the
-//    integer mantissa and exponent without the FP64 pipe), summed over 8
-//    steps in binary64 and carried into a per-lane double-double (Sec. 5).
+//  * Each step's signed term is split without rounding into a binary64 head
+//    (assembled from the integer mantissa and exponent) and a small tail, and
+//    added to a per-lane double-double with an exact TwoSum (Sec. 5's "quad"
+//    outer sum, applied to every term): the only roundings left are the
+//    62-bit products and the double-double itself.
 //  * The matrix is staged in shared memory as signed column increments
 //    (+D_j and -D_j, j < n-1), column-contiguous; all lanes of a warp flip the
 //    same column at the same step (aligned chunks, Sec. 3.1.1), so every
@@ -92,18 +94,28 @@ __device__ __forceinline__ void row_add(unsigned long long& Y, long long d, uint
       : "r"(dlo), "r"(dhi), "r"(one));
 }
 
-// Binary64 bit pattern of sign * M * 2^(f+1-1023-62) with M in [2^62, 2^63):
-// round to 53 bits, place the implicit bit on the exponent field (f is the
-// biased exponent minus one, clamped at 0 by the caller).
-__device__ __forceinline__ double prod_to_double(const Prod& p, uint32_t f, uint32_t signbit) {
+// The term sign * M * 2^(f+1-1023-62), M in [2^62, 2^63), as an unevaluated
+// sum hi + lo of two binary64 numbers with no rounding: hi is M rounded to 53
+// bits (the implicit bit placed on the exponent field f, the biased exponent
+// minus one, clamped at 0 by the caller), lo = M - round(M) in [-512, 511]
+// units of 2^(f+1-1023-62).  Both are assembled with integer operations; only
+// the small int -> binary64 conversion and the power-of-two scaling of lo use
+// the FP64 pipe.
+__device__ __forceinline__ void prod_to_dd(const Prod& p, uint32_t f, uint32_t signbit, double& hi, double& lo) {
   uint32_t rlo, rhi;
   asm("add.cc.u32 %0, %2, 512;\n\t"
       "addc.u32 %1, %3, 0;"
       : "=r"(rlo), "=r"(rhi)
       : "r"(p.m0), "r"(p.m1));
-  uint32_t lo32 = __funnelshift_r(rlo, rhi, 10);
-  uint32_t hi32 = (rhi >> 10) + (f << 20) + signbit;
-  return __hiloint2double((int)hi32, (int)lo32);
+  const uint32_t lo32 = __funnelshift_r(rlo, rhi, 10);
+  const uint32_t hi32 = (rhi >> 10) + (f << 20) + signbit;
+  hi = __hiloint2double((int)hi32, (int)lo32);
+  // remainder M - (R with its low 10 bits cleared), |r| <= 512, with the sign
+  const int32_t r = (int32_t)(p.m0 - (rlo & 0xFFFFFC00u));
+  const int32_t sr = signbit ? -r : r;
+  // 2^(f + 1 - 1023 - 62) as binary64: biased exponent f - 61 (0 flushes)
+  const int32_t fe = max((int32_t)f - 61, 0);
+  lo = (double)sr * __hiloint2double(fe << 20, 0);
 }
 
 // Shared-memory layout (dynamic): Dpm[(2j + s) * NP + i] for j < n-1,
@@ -195,7 +207,7 @@ __global__ void __launch_bounds__(kBlock, (N <= 48 ? 2 : 1)) ryser_real_kernel(R
   const long long* base = reinterpret_cast<const long long*>(smem + L::kBase);
   const long long* zero = reinterpret_cast<const long long*>(smem + L::kZero);
 
-  // exponent bookkeeping, see prod_to_double: the term is
+  // exponent bookkeeping, see prod_to_dd: the term is
   // sign * M * 2^(64N + 3 - sum_s - sum_lz - 62) in units of prod_i x_i.
   const int K1 = 64 * N + 1025 - sh.sum_s;
   const uint32_t one = (uint32_t)a.one;  // 1, opaque to the compiler
@@ -232,7 +244,6 @@ __global__ void __launch_bounds__(kBlock, (N <= 48 ? 2 : 1)) ryser_real_kernel(R
       for (int i = 0; i < N; ++i) Y[i] += (unsigned long long)(col[i] & msk);
     }
 
-    double bacc = 0.0;
     for (uint32_t t = 0; t < nsteps; ++t) {
       // column j = ctz(t) enters or leaves (Alg. 1: j = log2(Gray_t xor
       // Gray_{t-1}), entering iff bit j+1 of g is clear); t = 0 is the chunk's
@@ -264,14 +275,12 @@ __global__ void __launch_bounds__(kBlock, (N <= 48 ? 2 : 1)) ryser_real_kernel(R
       const int shifts = 30 * (N + 1) - (int)epos;
       const int f = K1 - shifts - (N + 1);
       const uint32_t signbit = (neg ^ t ^ gpar) << 31;
-      const double term = prod_to_double(pa, (uint32_t)max(f, 0), signbit);
-      if (t - tlo < tcnt) bacc += term;
-      if ((t & 7u) == 7u) {
-        acc = dd_add_d(acc, bacc);
-        bacc = 0.0;
-      }
+      double th, tl;
+      prod_to_dd(pa, (uint32_t)max(f, 0), signbit, th, tl);
+      const bool in = t - tlo < tcnt;
+      dd_acc(acc, in ? th : 0.0, in ? tl : 0.0);
     }
-    acc = dd_add_d(acc, bacc);
+    acc = dd_make(acc.hi, acc.lo);  // renormalise the lane partial
   }
 
   dd blk = dd_block_sum(acc);

@@ -1,0 +1,317 @@
+// Sparse real Ryser kernel (Alg. 2, SPARYSER, chunked as Alg. 3 with
+// power-of-two chunks, Sec. 3.1.1) on a CCS matrix (Fig. 1).
+//
+//  * Rows are scaled by a power of two and rounded once to 64-bit fixed point
+//    exactly as in the dense kernel, but without the odd-row trick, so a row
+//    value is exactly zero when the fixed-point sum is zero.
+//  * The row vector lives in shared memory, one int64 per (row, lane) with
+//    the lane index fastest (conflict-free), because the rows a column touches
+//    are only known at run time.  Each step applies only the nonzeros of the
+//    changed column (Alg. 2), from a per-column list staged in shared memory;
+//    all lanes of a warp walk the same list (aligned chunks), so the list
+//    reads are broadcasts.
+//  * Every lane counts its zero rows; while the count is positive the term is
+//    exactly zero and the product is skipped.
+//  * Products, exact per-step double-double accumulation and the fixed-order
+//    reduction are those of the dense real kernel.
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "real.cuh"
+
+namespace permgpu {
+
+constexpr int kSpBlock = 128;  // threads per CTA (row vector: n x 128 x 8 bytes)
+constexpr int kSpWarps = kSpBlock / 32;
+
+struct SpEntry {
+  int32_t row;
+  int32_t pad;
+  long long d;  // +2 Q_ij; the leaving sign is applied by negation
+};
+
+struct SpArgs {
+  const int32_t* cptrs;
+  const int32_t* rids;
+  const double* cvals;
+  int n;
+  int nnz;
+  int c;
+  int one;
+  uint64_t nchunks;
+  dd* part;
+  unsigned int* counter;
+  double* out;
+  int32_t* status;
+};
+
+struct SpShared {
+  int bad;
+  int zero_row;
+  int sum_s;
+  int bound_log2;
+};
+
+// Dynamic shared memory: cp[n+1] (int32, column pointers), ent[nnz] (SpEntry),
+// base[n] (int64), then the row vectors x[n][kSpBlock] (int64).
+__global__ void __launch_bounds__(kSpBlock) ryser_sparse_kernel(SpArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ SpShared sh;
+  __shared__ int s_scale[64];
+  const int n = a.n, nnz = a.nnz;
+  int32_t* cp = reinterpret_cast<int32_t*>(smem);
+  const size_t off_ent = ((sizeof(int32_t) * (n + 1) + 15) / 16) * 16;
+  SpEntry* ent = reinterpret_cast<SpEntry*>(smem + off_ent);
+  long long* base = reinterpret_cast<long long*>(smem + off_ent + sizeof(SpEntry) * nnz);
+  long long* xs = base + n;  // x[i * kSpBlock + tid]
+
+  if (threadIdx.x == 0) {
+    sh.bad = 0;
+    sh.zero_row = 0;
+    sh.sum_s = 0;
+    sh.bound_log2 = 0;
+  }
+  __syncthreads();
+  // structure checks (Fig. 1): cptrs[0] = 0, cptrs[n] = nnz, monotone, rows in
+  // range and strictly increasing within a column, finite values
+  for (int j = threadIdx.x; j <= n; j += kSpBlock) {
+    int v = a.cptrs[j];
+    cp[j] = v;
+    if ((j == 0 && v != 0) || (j == n && v != nnz) || v < 0 || v > nnz) atomicOr(&sh.bad, 1);
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < n; j += kSpBlock) {
+    if (cp[j] > cp[j + 1]) atomicOr(&sh.bad, 1);
+  }
+  __syncthreads();
+  if (!sh.bad) {
+    for (int j = threadIdx.x; j < n; j += kSpBlock)
+      for (int p = cp[j]; p < cp[j + 1]; ++p) {
+        int r = a.rids[p];
+        double v = a.cvals[p];
+        if (r < 0 || r >= n || (p > cp[j] && r <= a.rids[p - 1]) || !isfinite(v)) atomicOr(&sh.bad, 1);
+      }
+  }
+  __syncthreads();
+  // row scales: thread i scans every column for row i (deterministic sums)
+  if (!sh.bad && threadIdx.x < n) {
+    const int i = threadIdx.x;
+    double absum = 0.0;
+    for (int j = 0; j < n; ++j)
+      for (int p = cp[j]; p < cp[j + 1]; ++p)
+        if (a.rids[p] == i) absum += fabs(a.cvals[p]);
+    int k = 0;
+    if (absum > 0.0) frexp(absum, &k);
+    else atomicOr(&sh.zero_row, 1);
+    s_scale[i] = 61 - k;
+    atomicAdd(&sh.sum_s, 61 - k);
+    atomicAdd(&sh.bound_log2, k - 1);
+  }
+  __syncthreads();
+  // column entries (2 Q_ij) and base_i = Q_{i,n-1} - sum_{j<n-1} Q_ij
+  if (!sh.bad) {
+    for (int p = threadIdx.x; p < nnz; p += kSpBlock) {
+      int r = a.rids[p];
+      long long q = __double2ll_rn(ldexp(a.cvals[p], s_scale[r]));
+      ent[p].row = r;
+      ent[p].pad = 0;
+      ent[p].d = 2 * q;
+    }
+  }
+  __syncthreads();
+  if (!sh.bad && threadIdx.x < n) {
+    const int i = threadIdx.x;
+    long long b = 0;
+    for (int j = 0; j < n; ++j)
+      for (int p = cp[j]; p < cp[j + 1]; ++p)
+        if (ent[p].row == i) b += (j == n - 1) ? ent[p].d / 2 : -(ent[p].d / 2);
+    base[i] = b;
+  }
+  __syncthreads();
+
+  const bool skip = sh.bad || sh.zero_row || sh.bound_log2 + n > 1000;
+  const int K1 = 64 * n + 1025 - sh.sum_s;
+  const uint32_t one = (uint32_t)a.one;
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const uint64_t warp_id = (uint64_t)(blockIdx.x * kSpBlock + tid) >> 5;
+  const uint64_t nwarps = (uint64_t)(gridDim.x * kSpBlock) >> 5;
+  const uint64_t ngroups = skip ? 0 : (a.nchunks + 31) / 32;
+  const uint32_t nsteps = 1u << a.c;
+  dd acc = {0.0, 0.0};
+
+  for (uint64_t q = warp_id; q < ngroups; q += nwarps) {
+    const uint64_t k = q * 32 + lane;
+    const bool active = k < a.nchunks;
+    const uint64_t g0 = k << a.c;
+    const uint32_t kb = (uint32_t)(k & 1u) << a.c;
+    const uint32_t gpar = (uint32_t)(g0 & 1u);
+    // x at Gray(g0) and its zero count
+    for (int i = 0; i < n; ++i) xs[i * kSpBlock + tid] = base[i];
+    const uint64_t G = gray64(g0);
+    for (int j = (a.c > 0 ? a.c - 1 : 0); j < n - 1; ++j) {
+      if ((G >> j) & 1u)
+        for (int p = cp[j]; p < cp[j + 1]; ++p) xs[ent[p].row * kSpBlock + tid] += ent[p].d;
+    }
+    int zeros = 0;
+    for (int i = 0; i < n; ++i) zeros += xs[i * kSpBlock + tid] == 0;
+
+    for (uint32_t t = 0; t < nsteps; ++t) {
+      if (t) {
+        const int j = __ffs(t) - 1;
+        const bool leave = ((t | kb) >> (j + 1)) & 1u;
+        for (int p = cp[j]; p < cp[j + 1]; ++p) {  // Alg. 2: nonzeros of column j only
+          const SpEntry e = ent[p];
+          long long* xp = xs + e.row * kSpBlock + tid;
+          const long long old = *xp;
+          const long long nv = leave ? old - e.d : old + e.d;
+          *xp = nv;
+          zeros += (nv == 0) - (old == 0);
+        }
+      }
+      if (zeros == 0 && active) {
+        Prod pa, pb;
+        prod_init(pa);
+        prod_init(pb);
+        uint32_t neg = 0, epos = 0;
+        int i = 0;
+        for (; i + 1 < n; i += 2) {
+          const long long ya = xs[i * kSpBlock + tid], yb = xs[(i + 1) * kSpBlock + tid];
+          const uint32_t ma = (uint32_t)(ya >> 63), mb = (uint32_t)(yb >> 63);
+          const unsigned long long aa = (unsigned long long)((ya ^ (long long)(int32_t)ma) - (long long)(int32_t)ma);
+          const unsigned long long ab = (unsigned long long)((yb ^ (long long)(int32_t)mb) - (long long)(int32_t)mb);
+          neg = neg + ma + mb;
+          epos += prod_mul(pa, (uint32_t)aa, (uint32_t)(aa >> 32));
+          epos += prod_mul(pb, (uint32_t)ab, (uint32_t)(ab >> 32));
+        }
+        if (i < n) {
+          const long long ya = xs[i * kSpBlock + tid];
+          const uint32_t ma = (uint32_t)(ya >> 63);
+          const unsigned long long aa = (unsigned long long)((ya ^ (long long)(int32_t)ma) - (long long)(int32_t)ma);
+          neg += ma;
+          epos += prod_mul(pa, (uint32_t)aa, (uint32_t)(aa >> 32));
+        }
+        epos += prod_mul(pa, pb.m0, pb.m1);
+        const int shifts = 30 * (n + 1) - (int)epos;
+        const int f = K1 - shifts - (n + 1);
+        const uint32_t signbit = (neg ^ t ^ gpar) << 31;
+        double th, tl;
+        prod_to_dd(pa, (uint32_t)max(f, 0), signbit, th, tl);
+        dd_acc(acc, th, tl);
+      }
+    }
+    acc = dd_make(acc.hi, acc.lo);
+  }
+
+  // reduction (fixed order): warps -> CTA -> last CTA
+  __shared__ dd s_w[kSpWarps];
+  dd v = dd_warp_sum(acc);
+  if (lane == 0) s_w[tid >> 5] = v;
+  __syncthreads();
+  if (tid == 0) {
+    dd b = {0.0, 0.0};
+    for (int w = 0; w < kSpWarps; ++w) b = dd_add(b, s_w[w]);
+    a.part[blockIdx.x] = b;
+  }
+  if (!arrive_last(a.counter)) return;
+  if (tid < 32) {
+    dd tot = dd_sum_partials(a.part, gridDim.x);
+    if (tid == 0) {
+      int32_t st = PERM_OK;
+      if (sh.bad) st = PERM_EINVAL;
+      else if (!sh.zero_row && sh.bound_log2 + n > 1000) st = PERM_ERANGE;
+      const double f = (n & 1) ? 2.0 : -2.0;
+      a.out[0] = st != PERM_OK ? __longlong_as_double(0x7ff8000000000000ll)
+                 : (sh.zero_row ? 0.0 : (tot.hi + tot.lo) * f);
+      if (a.status) *a.status = st;
+      *a.counter = 0u;
+    }
+  }
+}
+
+__global__ void sparse_trivial_kernel(double* out, int32_t* status) {
+  if (threadIdx.x == 0) {
+    out[0] = 1.0;
+    if (status) *status = PERM_OK;
+  }
+}
+
+}  // namespace permgpu
+
+using namespace permgpu;
+
+extern "C" int perm_sparse(int n, const int32_t* cptrs, const int32_t* rids, const double* cvals, int64_t nnz,
+                           double* out, int32_t* status, void* stream) {
+  if (n < 0 || n > PERM_NMAX) return PERM_ERANGE;
+  if (!out || (n > 0 && !cptrs) || nnz < 0 || nnz > (int64_t)n * n || (nnz > 0 && (!rids || !cvals)))
+    return PERM_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (n == 0) {
+    sparse_trivial_kernel<<<1, 32, 0, s>>>(out, status);
+    return cudaGetLastError() == cudaSuccess ? PERM_OK : PERM_ECUDA;
+  }
+  const size_t off_ent = ((sizeof(int32_t) * (n + 1) + 15) / 16) * 16;
+  const size_t smem = off_ent + sizeof(SpEntry) * (size_t)nnz + sizeof(long long) * n +
+                      sizeof(long long) * (size_t)n * kSpBlock;
+  static std::mutex mu;
+  int nb = 0, dev = 0, sms = 0;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (cudaFuncSetAttribute(ryser_sparse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      return PERM_ERANGE;  // does not fit shared memory
+    }
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, ryser_sparse_kernel, kSpBlock, smem) != cudaSuccess ||
+        nb <= 0)
+      return PERM_ECUDA;
+  }
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return PERM_ECUDA;
+  const uint64_t N = 1ull << (n - 1);
+  const int grid_full = sms * nb;
+  const int c = plan_chunk_exponent(n, N, grid_full * kSpWarps);
+  const uint64_t nchunks = N >> c;
+  const uint64_t need = ((nchunks + 31) / 32 + kSpWarps - 1) / kSpWarps;
+  const int grid = (int)(need < (uint64_t)grid_full ? (need > 0 ? need : 1) : grid_full);
+  void* ws = nullptr;
+  const size_t bytes = sizeof(dd) * (size_t)grid + 16;
+  if (cudaMallocAsync(&ws, bytes, s) != cudaSuccess) {
+    cudaGetLastError();
+    return PERM_ENOMEM;
+  }
+  unsigned int* counter = reinterpret_cast<unsigned int*>(static_cast<char*>(ws) + sizeof(dd) * (size_t)grid);
+  if (cudaMemsetAsync(counter, 0, sizeof(unsigned int), s) != cudaSuccess) {
+    cudaFreeAsync(ws, s);
+    return PERM_ECUDA;
+  }
+  SpArgs args;
+  memset(&args, 0, sizeof(args));
+  args.cptrs = cptrs;
+  args.rids = rids;
+  args.cvals = cvals;
+  args.n = n;
+  args.nnz = (int)nnz;
+  args.c = c;
+  args.one = 1;
+  args.nchunks = nchunks;
+  args.part = static_cast<dd*>(ws);
+  args.counter = counter;
+  args.out = out;
+  args.status = status;
+  void* params[] = {&args};
+  cudaError_t e = cudaLaunchKernel(reinterpret_cast<const void*>(ryser_sparse_kernel), dim3(grid), dim3(kSpBlock),
+                                   params, smem, s);
+  cudaError_t f = cudaFreeAsync(ws, s);
+  if (e != cudaSuccess || f != cudaSuccess) {
+    cudaGetLastError();
+    return PERM_ECUDA;
+  }
+  return PERM_OK;
+}

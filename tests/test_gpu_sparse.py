@@ -1,0 +1,98 @@
+"""Parity of the sparse CCS path (Alg. 2 with zero-skip, C ABI, GB300) with
+the oracle.  Positive values: relative 1e-10 bar, tighter checks as for the
+dense real path."""
+import math
+
+import numpy as np
+import pytest
+
+import synthetic as syn
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pg():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2502_16577_gb300 as pg
+    from paper_2502_16577_gb300 import build
+
+    build.build()
+    pg.load()
+    return pg
+
+
+def _ccs(A):
+    import torch
+
+    cp, ri, cv = syn.to_ccs(A)
+    return (A.shape[0], torch.from_numpy(cp).cuda(), torch.from_numpy(ri).cuda(), torch.from_numpy(cv).cuda())
+
+
+@pytest.mark.parametrize("n,density", [(1, 1.0), (2, 0.9), (5, 0.5), (9, 0.35), (14, 0.25), (19, 0.2), (22, 0.2)])
+def test_vs_oracle(pg, oracle, n, density):
+    A = syn.sparse_real(n, 9100 + n, density)
+    got = pg.perm_sparse(*_ccs(A))
+    crs, ccs = oracle.to_crs_ccs(A)
+    want_alg2 = oracle.perm_sparse(n, crs, ccs)
+    want_dp = oracle.perm_dp_f64(A)
+    assert got == pytest.approx(want_dp, rel=1e-10)
+    assert got == pytest.approx(want_dp, rel=1e-13)
+    assert got == pytest.approx(want_alg2, rel=1e-12)
+
+
+def test_signed_and_zero_heavy(pg, oracle):
+    # integer-valued sparse matrices: many exact zeros in x, the skip fires
+    for seed, n in ((1, 12), (2, 17), (3, 20)):
+        M = syn.bernoulli01(n, seed, 0.3).astype(float)
+        M[np.arange(n), np.arange(n)] = 1.0
+        got = pg.perm_sparse(*_ccs(M))
+        assert got == pytest.approx(oracle.perm_dp_bin(M.astype(np.uint8)), rel=1e-15)
+        S = syn.sparse_real(n, 50 + seed, 0.3) * np.where(syn.bernoulli01(n, 60 + seed) > 0, 1.0, -1.0)
+        want = oracle.perm_dp_f64(S)
+        assert abs(pg.perm_sparse(*_ccs(S)) - want) <= 1e-13 * oracle.perm_dp_f64(np.abs(S))
+
+
+def test_matches_dense_path(pg):
+    import torch
+
+    A = syn.sparse_real(26, 777, 0.25)
+    dense = pg.perm(torch.from_numpy(A).cuda())
+    assert pg.perm_sparse(*_ccs(A)) == pytest.approx(dense, rel=1e-13)
+
+
+def test_tridiagonal_n44_full_size(pg, oracle):
+    """Full 2^43-step sweep of the n = 44 tridiagonal all-ones matrix:
+    perm = F_45 exactly (the zero-skip makes most steps cheap)."""
+    n = 44
+    got = pg.perm_sparse(*_ccs(syn.tridiagonal_ones(n).astype(float)))
+    assert got == float(oracle.fibonacci(n + 1))
+
+
+def test_block_diagonal_n32(pg, oracle):
+    B1, B2 = syn.sparse_real(16, 1, 0.3), syn.sparse_real(16, 2, 0.3)
+    M = syn.shuffle_rows_cols(syn.block_diagonal([B1, B2]), 3)
+    want = oracle.perm_dp_f64(B1) * oracle.perm_dp_f64(B2)
+    assert pg.perm_sparse(*_ccs(M)) == pytest.approx(want, rel=1e-12)
+
+
+def test_malformed_ccs_is_rejected(pg):
+    import torch
+
+    n = 4
+    ok = syn.sparse_real(n, 5, 0.6)
+    _, cp, ri, cv = _ccs(ok)
+    bad_rows = ri.clone()
+    bad_rows[0] = 9  # out of range
+    with pytest.raises(pg.PermError) as e:
+        pg.perm_sparse(n, cp, bad_rows, cv)
+    assert e.value.code == 1
+    bad_ptr = cp.clone()
+    bad_ptr[1] = bad_ptr[2] + 1  # not monotone
+    with pytest.raises(pg.PermError):
+        pg.perm_sparse(n, bad_ptr, ri, cv)
+    Z = ok.copy()
+    Z[2] = 0.0
+    assert pg.perm_sparse(*_ccs(Z)) == 0.0
