@@ -139,6 +139,24 @@ int perm_sparse(int n, const int32_t* cptrs, const int32_t* rids, const double* 
 int perm_host(const void* A_host, int n, int type, void* out_host, void* stream);
 
 /*
+ * perm_f64_noalloc - perm(A, n, PERM_F64, out, status, stream) without any
+ * allocation.  The paper has no counterpart: this entry point exists for
+ * callers that may not call the CUDA allocator, e.g. code running under a
+ * framework that has reserved all device memory for its own pool, or loops
+ * that forbid allocation once they have started.  Arguments, results and
+ * *status are those of perm() for real matrices.
+ *
+ * Its scratch is a fixed 64 KiB array in the library's device memory (room
+ * for 4096 CTA partials); a launch that would need more returns PERM_ENOMEM
+ * before doing anything.  The array is shared by every call on a device and
+ * keeps the last call's contents: calls whose work overlaps on the GPU
+ * (other streams, unordered host threads) race on it and must be ordered by
+ * the caller.  The first call on each device looks the array up with
+ * cudaGetSymbolAddress; make that first call before any stream capture.
+ */
+int perm_f64_noalloc(const double* A, int n, double* out, int32_t* status, void* stream);
+
+/*
  * perm_pipe_peaks - measured throughput of the pipes the kernels use, the
  * denominators of the benchmark's roofline fractions (measurement
  * infrastructure; the paper has no counterpart).  Runs microbenchmarks on the
