@@ -120,14 +120,6 @@ def _cuda_ok() -> bool:
         return False
 
 
-def shard(n_steps: int, rank: int, world: int):
-    """Contiguous share of [0, n_steps) for one rank (Sec. 6.3: the iteration
-    space is first split per GPU)."""
-    base, rem = divmod(n_steps, world)
-    lo = rank * base + min(rank, rem)
-    return lo, lo + base + (1 if rank < rem else 0)
-
-
 # ---------------------------------------------------------------- CPU oracle
 
 def oracle_sample(frac_log2: int, threads: int):
@@ -209,6 +201,7 @@ def run_gpu(args):
     import torch
 
     import paper_2502_16577_gb300 as pg
+    from paper_2502_16577_gb300 import ranges
 
     rank, world, local, dist = dist_setup(args.gpus)
     torch.cuda.set_device(local)
@@ -219,7 +212,7 @@ def run_gpu(args):
     for name, A in workloads():
         t = torch.from_numpy(np.ascontiguousarray(A)).to(dev)
         n = A.shape[0]
-        lo, hi = shard(steps_of(n), rank, world)
+        lo, hi = ranges.shard(steps_of(n), rank, world)
         typ = pg.perm_type_of(t.dtype)
         words = {pg.PERM_F64: 2, pg.PERM_C128: 4, pg.PERM_BIN: 3}[typ]
         out = torch.zeros(words, dtype=torch.int64 if typ == pg.PERM_BIN else torch.float64, device=dev)
@@ -246,13 +239,12 @@ def run_gpu(args):
             if world == 1:
                 results[m["name"]] = m["out"].cpu().numpy().copy()
                 continue
-            parts = [torch.zeros_like(m["out"]) for _ in range(world)]
-            dist.all_gather(parts, m["out"])
+            o = m["out"].cpu().numpy()
+            local_part = sum((int(w) % (1 << 64)) << (64 * i) for i, w in enumerate(o)) \
+                if m["type"] == pg.PERM_BIN else tuple(float(v) for v in o)
+            parts = ranges.gather_partials(dist, m["type"], local_part)
             if rank == 0:
-                vals = [p.cpu().numpy() for p in parts]
-                if m["type"] == pg.PERM_BIN:
-                    vals = [sum(int(w) % (1 << 64) << (64 * i) for i, w in enumerate(v)) for v in vals]
-                results[m["name"]] = pg.perm_combine(m["type"], m["n"], vals)
+                results[m["name"]] = pg.perm_combine(m["type"], m["n"], parts)
         return results
 
     # warm-up (untimed)

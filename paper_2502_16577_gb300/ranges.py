@@ -1,0 +1,110 @@
+"""Host-side logic of splitting a Gray-code sweep across GPUs, processes or
+time (Secs. 3.3 and 6.3: the iteration space is split first per GPU, and the
+only exchange is the final sum of partials).
+
+* shard: the contiguous share of [0, 2^(n-1)) that one of `world` ranks owns;
+* gather_partials: the single exchange, one all_gather of each rank's partial
+  (16-48 bytes) over an initialised torch.distributed group;
+* checkpoint / restore: completed ranges with their exact partials as JSON
+  (binary64 words as hex), so a long sweep resumes where it stopped and the
+  combined result is bit-identical to an uninterrupted run.
+"""
+from __future__ import annotations
+
+import json
+
+from ._lib import PERM_BIN, PERM_C128, PERM_F64
+
+WORDS = {PERM_F64: 2, PERM_C128: 4, PERM_BIN: 3}
+
+
+def total_steps(n: int) -> int:
+    return 1 << (n - 1) if n > 0 else 0
+
+
+def shard(n_steps: int, rank: int, world: int):
+    """[lo, hi) of rank `rank` out of `world`: contiguous, sizes differ by at most 1."""
+    if world < 1 or not 0 <= rank < world:
+        raise ValueError("bad rank / world")
+    base, rem = divmod(n_steps, world)
+    lo = rank * base + min(rank, rem)
+    return lo, lo + base + (1 if rank < rem else 0)
+
+
+def split(n_steps: int, parts: int):
+    return [shard(n_steps, r, parts) for r in range(parts)]
+
+
+def check_cover(ranges, n_steps: int) -> None:
+    """The ranges must tile [0, n_steps) exactly once (any order)."""
+    pos = 0
+    for lo, hi in sorted(ranges):
+        if lo != pos or hi < lo:
+            raise ValueError(f"ranges do not tile [0, {n_steps}): gap or overlap at {pos}")
+        pos = hi
+    if pos != n_steps:
+        raise ValueError(f"ranges stop at {pos}, not {n_steps}")
+
+
+def partial_to_words(t: int, value):
+    """A perm_range partial (tuple of floats, or an int for 0/1) as JSON-safe words."""
+    if t == PERM_BIN:
+        v = int(value) % (1 << 192)
+        return [format(v, "048x")]
+    return [float(x).hex() for x in value]
+
+
+def words_to_partial(t: int, words):
+    if t == PERM_BIN:
+        return int(words[0], 16)
+    return tuple(float.fromhex(w) for w in words)
+
+
+def checkpoint(t: int, n: int, done) -> str:
+    """JSON of completed (lo, hi, partial) triples."""
+    return json.dumps({"type": int(t), "n": int(n),
+                       "done": [[int(lo), int(hi), partial_to_words(t, p)] for lo, hi, p in done]})
+
+
+def restore(text: str):
+    d = json.loads(text)
+    t = int(d["type"])
+    return t, int(d["n"]), [(lo, hi, words_to_partial(t, w)) for lo, hi, w in d["done"]]
+
+
+def remaining(n: int, done):
+    """Ranges of [0, 2^(n-1)) not yet covered by done (lo, hi, partial) triples."""
+    out, pos = [], 0
+    for lo, hi, _ in sorted(done, key=lambda x: x[0]):
+        if lo > pos:
+            out.append((pos, lo))
+        pos = max(pos, hi)
+    if pos < total_steps(n):
+        out.append((pos, total_steps(n)))
+    return out
+
+
+def gather_partials(dist, t: int, partial_words):
+    """All-gather each rank's partial (a list of 64-bit words) with torch.distributed;
+    returns the list of partials in rank order on every rank."""
+    import torch
+
+    w = WORDS[t]
+    if t == PERM_BIN:
+        v = int(partial_words) % (1 << 192)
+        local = torch.tensor([((v >> (64 * k)) & 0xFFFFFFFFFFFFFFFF) - (1 << 64 if (v >> (64 * k + 63)) & 1 else 0)
+                              for k in range(w)], dtype=torch.int64)
+    else:
+        local = torch.tensor(list(partial_words), dtype=torch.float64)
+    backend_dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    local = local.to(backend_dev)
+    parts = [torch.zeros_like(local) for _ in range(dist.get_world_size())]
+    dist.all_gather(parts, local)
+    out = []
+    for p in parts:
+        p = p.cpu().tolist()
+        if t == PERM_BIN:
+            out.append(sum((int(x) % (1 << 64)) << (64 * k) for k, x in enumerate(p)))
+        else:
+            out.append(tuple(p))
+    return out
