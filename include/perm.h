@@ -132,6 +132,43 @@ int perm_sparse(int n, const int32_t* cptrs, const int32_t* rids, const double* 
                 double* out, int32_t* status, void* stream);
 
 /*
+ * Batched complex permanents (boson-sampling style: thousands of small k x k
+ * matrices of uneven sizes).  Each matrix is the sweep of perm() (Alg. 1 over
+ * complex entries, Alg. 3 chunks of Sec. 3.1.1); all of them run in one
+ * CUDA-graph replay: a prep kernel (fixed-point tables), one persistent
+ * kernel that pops work items (32 matrices of one size per warp for short
+ * sweeps, 32 aligned Gray chunks of one matrix per warp for long ones,
+ * longest first) from an atomic counter, and a finish kernel that adds each
+ * matrix's item partials in a fixed order.
+ *
+ * perm_batched_plan_create - build a plan (host call; allocates the plan's
+ *   device buffers and captures the graph; synchronous).
+ *     type       PERM_C128 (the only batched type).
+ *     ns_host    host int[count], sizes k in 1..32.
+ *     A_packed   device double pairs: matrix m, row-major, starts at complex
+ *                element offsets_host[m] (host int64[count]).
+ *     out        device double[2*count]: (re, im) of perm of every matrix.
+ *     status     device int32[count] or NULL (perm() status per matrix).
+ *   A_packed, out and status are bound to the plan: every perm_batched()
+ *   replay reads and writes these buffers.
+ * perm_batched - replay the plan's graph on stream (allocates nothing).
+ * perm_batched_autotune - time the candidate chunk exponents and the
+ *   one-matrix-per-lane mode of every size class on the plan's own matrices
+ *   (rounds timed runs each), keep the fastest, rebuild the queue and
+ *   recapture.  Overwrites out.  Synchronous.
+ * perm_batched_plan_info - the choice for size k: *mode (1 = one matrix per
+ *   lane, 0 = chunked), *c (chunk exponent), *nitems (queue length).
+ * perm_batched_plan_destroy - free the plan (NULL is ignored).
+ */
+typedef struct perm_batch_plan perm_batch_plan;
+int perm_batched_plan_create(perm_batch_plan** plan, int type, const int* ns_host, int count, const void* A_packed,
+                             const int64_t* offsets_host, void* out, int32_t* status);
+int perm_batched(perm_batch_plan* plan, void* stream);
+int perm_batched_autotune(perm_batch_plan* plan, int rounds, void* stream);
+int perm_batched_plan_info(const perm_batch_plan* plan, int k, int* mode, int* c, int* nitems);
+void perm_batched_plan_destroy(perm_batch_plan* plan);
+
+/*
  * perm_host - perm() on host buffers: copies A in, runs perm() on stream,
  * copies the result out and waits.  Returns the device status as well.
  *   A_host   host, layout as perm()'s A;  out_host  host, layout as perm()'s out.

@@ -21,7 +21,7 @@ import numpy as np
 from . import _lib
 from ._lib import PERM_BIN, PERM_C128, PERM_F64, PermError, check, load
 
-__all__ = ["perm", "perm_async", "perm_range", "perm_range_async", "perm_combine", "perm_sparse", "perm_sparse_async", "perm_host", "pipe_peaks", "perm_type_of", "PermError",
+__all__ = ["perm", "perm_async", "perm_range", "perm_range_async", "perm_combine", "perm_sparse", "perm_sparse_async", "perm_host", "pipe_peaks", "BatchPlan", "perm_type_of", "PermError",
            "PERM_F64", "PERM_C128", "PERM_BIN", "load"]
 
 
@@ -191,6 +191,74 @@ def perm_sparse(n: int, cptrs, rids, cvals, stream=None) -> float:
     s.synchronize()
     check(int(status.item()), "perm_sparse")
     return float(out.item())
+
+
+class BatchPlan:
+    """A batched plan over a list of square complex128 matrices (perm_batched_*).
+
+    The matrices are packed into one device buffer owned by the plan; run()
+    replays the captured graph (one launch) and returns the device results."""
+
+    def __init__(self, mats, device=None, autotune_rounds: int = 0, stream=None):
+        torch = _torch()
+        lib = load()
+        device = device or torch.device("cuda")
+        ks = [int(m.shape[0]) for m in mats]
+        offs, total = [], 0
+        for k in ks:
+            offs.append(total)
+            total += k * k
+        host = np.zeros(total, dtype=np.complex128)
+        for m, o in zip(mats, offs):
+            a = m.detach().cpu().numpy() if hasattr(m, "detach") else np.asarray(m)
+            host[o:o + a.size] = np.asarray(a, dtype=np.complex128).reshape(-1)
+        self.A = torch.from_numpy(host).to(device)
+        self.out = torch.zeros(2 * len(ks), dtype=torch.float64, device=device)
+        self.status = torch.full((len(ks),), -1, dtype=torch.int32, device=device)
+        self.ks = ks
+        self._plan = ctypes.c_void_p(0)
+        karr = (ctypes.c_int * len(ks))(*ks)
+        oarr = (ctypes.c_int64 * len(ks))(*offs)
+        check(lib.perm_batched_plan_create(ctypes.byref(self._plan), PERM_C128, karr, len(ks),
+                                           ctypes.c_void_p(self.A.data_ptr()), oarr,
+                                           ctypes.c_void_p(self.out.data_ptr()),
+                                           ctypes.c_void_p(self.status.data_ptr())), "perm_batched_plan_create")
+        if autotune_rounds:
+            h, _ = _stream_handle(stream)
+            check(lib.perm_batched_autotune(self._plan, int(autotune_rounds), h), "perm_batched_autotune")
+
+    def run_async(self, stream=None) -> None:
+        h, _ = _stream_handle(stream)
+        check(load().perm_batched(self._plan, h), "perm_batched")
+
+    def run(self, stream=None):
+        """Replay and return a numpy complex128 array of the permanents."""
+        self.run_async(stream)
+        _, s = _stream_handle(stream)
+        s.synchronize()
+        st = self.status.cpu().numpy()
+        bad = np.nonzero(st != 0)[0]
+        if len(bad):
+            check(int(st[bad[0]]), f"perm_batched (matrix {int(bad[0])})")
+        o = self.out.cpu().numpy()
+        return o[0::2] + 1j * o[1::2]
+
+    def info(self, k: int):
+        mode, c, n = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        check(load().perm_batched_plan_info(self._plan, int(k), ctypes.byref(mode), ctypes.byref(c), ctypes.byref(n)),
+              "perm_batched_plan_info")
+        return {"mode": "lane" if mode.value == 1 else "chunks", "c": c.value, "items": n.value}
+
+    def close(self):
+        if self._plan:
+            load().perm_batched_plan_destroy(self._plan)
+            self._plan = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 PIPE_NAMES = ("fp64_fma", "fp64_add", "imad", "imad_wide", "shf")

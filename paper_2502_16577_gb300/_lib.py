@@ -18,7 +18,8 @@ _i32p = ctypes.POINTER(ctypes.c_int32)
 _lib = None
 
 SYMBOLS = ("perm", "perm_range", "perm_combine", "perm_sparse", "perm_host", "perm_pipe_peaks",
-           "perm_status_string", "perm_abi_version")
+           "perm_batched_plan_create", "perm_batched", "perm_batched_autotune", "perm_batched_plan_info",
+           "perm_batched_plan_destroy", "perm_status_string", "perm_abi_version")
 
 
 class PermError(RuntimeError):
@@ -50,6 +51,18 @@ def load(build_if_missing: bool = False):
     lib.perm_combine.argtypes = [ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, _vp]
     lib.perm_sparse.restype = ctypes.c_int
     lib.perm_sparse.argtypes = [ctypes.c_int, _vp, _vp, _vp, ctypes.c_int64, _vp, _vp, _vp]
+    lib.perm_batched_plan_create.restype = ctypes.c_int
+    lib.perm_batched_plan_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                             ctypes.c_int, _vp, ctypes.POINTER(ctypes.c_int64), _vp, _vp]
+    lib.perm_batched.restype = ctypes.c_int
+    lib.perm_batched.argtypes = [_vp, _vp]
+    lib.perm_batched_autotune.restype = ctypes.c_int
+    lib.perm_batched_autotune.argtypes = [_vp, ctypes.c_int, _vp]
+    lib.perm_batched_plan_info.restype = ctypes.c_int
+    lib.perm_batched_plan_info.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                           ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    lib.perm_batched_plan_destroy.restype = None
+    lib.perm_batched_plan_destroy.argtypes = [_vp]
     lib.perm_host.restype = ctypes.c_int
     lib.perm_host.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp]
     lib.perm_pipe_peaks.restype = ctypes.c_int

@@ -1,0 +1,627 @@
+// Batched complex permanents: thousands of k x k matrices of uneven sizes in
+// one CUDA-graph replay (prep kernel, one persistent work-queue kernel,
+// finish kernel).  Each matrix is the Ryser / Nijenhuis-Wilf sweep of the
+// single-matrix complex kernel (Alg. 1 over complex entries, chunked as
+// Alg. 3 with power-of-two chunks, Sec. 3.1.1):
+//
+//  * The plan (host) groups matrices by size k and builds a work queue:
+//    small k run one matrix per lane (32 matrices of equal k per warp item,
+//    the lanes walk the same Gray sequence), large k are cut into aligned
+//    chunks of 2^c steps, 32 chunks per warp item.  Items are ordered longest
+//    first (LPT) and warps pop them from one atomic counter.
+//  * The chunk exponent and the lane/warp mode of every size class come from
+//    a heuristic or from perm_batched_autotune, which times the candidates
+//    on the plan's own matrices.
+//  * The prep kernel rounds every matrix once to fixed point (as the
+//    single-matrix kernel) into a plan-owned table that the main kernel reads
+//    through L1 (column reads are warp broadcasts in the chunked mode).
+//  * Every item writes its partial to its own slot; the finish kernel adds a
+//    matrix's slots in a fixed order (deterministic), scales by 2 (-1)^(k-1)
+//    and writes the result.  Execution allocates nothing.
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+#include "common.cuh"
+#include "complex.cuh"
+#include "kernels.h"
+
+namespace permgpu {
+
+constexpr int kBatchKMax = 32;
+constexpr int kLaneMode = 1, kWarpMode = 0;
+
+struct BatchMat {
+  int32_t k;
+  int32_t sum_s;
+  int32_t flags;  // 1: non-finite entry, 2: zero row, 4: exponent range
+  int32_t slot0;  // first partial slot of this matrix
+  int64_t a_off;  // element offset of the matrix in the packed input
+  int64_t d_off;  // longlong2 offset of its table (D, base, zero) in the plan
+};
+
+struct BatchItem {
+  int32_t mode;   // kLaneMode or kWarpMode
+  int32_t k;
+  int32_t c;      // chunk exponent (warp mode)
+  int32_t count;  // lane mode: matrices in this item (<= 32)
+  int32_t mat;    // lane mode: first index into lane_mats; warp mode: the matrix
+  int32_t slot;   // warp mode: the partial slot of this item
+  int64_t chunk0; // warp mode: first chunk
+};
+
+struct BatchArgs {
+  const double* A;        // packed (re, im) pairs
+  const BatchMat* mats;
+  const BatchItem* items;
+  const int32_t* lane_mats;
+  longlong2* table;
+  dd* slots;              // 2 per slot (re, im)
+  unsigned int* counter;
+  double* out;            // (re, im) per matrix
+  int32_t* status;        // per matrix (optional)
+  int nmats;
+  int nitems;
+};
+
+// One CTA per matrix: D[(2j+s) k + i], base[k], zero[k] as in cplx_stage.
+__global__ void __launch_bounds__(kBlock) batch_prep_kernel(BatchArgs a) {
+  const int m = blockIdx.x;
+  if (m >= a.nmats) return;
+  const BatchMat bm = a.mats[m];
+  const int k = bm.k;
+  longlong2* D = a.table + bm.d_off;
+  longlong2* base = D + (size_t)2 * (k > 1 ? k - 1 : 0) * k;
+  longlong2* zero = base + k;
+  __shared__ int s_sum, s_bound, s_flags;
+  if (threadIdx.x == 0) {
+    s_sum = 0;
+    s_bound = 0;
+    s_flags = 0;
+  }
+  __syncthreads();
+  const int i = threadIdx.x;
+  if (i < k) {
+    const double* row = a.A + 2 * (bm.a_off + (int64_t)i * k);
+    double absum = 0.0;
+    int fin = 1;
+    for (int j = 0; j < 2 * k; ++j) {
+      double v = row[j];
+      fin &= isfinite(v) ? 1 : 0;
+      absum += fabs(v);
+    }
+    int kk = 0;
+    if (fin && absum > 0.0) frexp(absum, &kk);
+    const int s = 60 - kk;
+    long long sr = 0, si = 0;
+    for (int j = 0; j < k - 1; ++j) {
+      long long qr = fin ? __double2ll_rn(ldexp(row[2 * j], s)) : 0;
+      long long qi = fin ? __double2ll_rn(ldexp(row[2 * j + 1], s)) : 0;
+      sr += qr;
+      si += qi;
+      D[(2 * j) * k + i] = make_longlong2(2 * qr, 2 * qi);
+      D[(2 * j + 1) * k + i] = make_longlong2(-2 * qr, -2 * qi);
+    }
+    long long nr = fin ? __double2ll_rn(ldexp(row[2 * (k - 1)], s)) : 0;
+    long long ni = fin ? __double2ll_rn(ldexp(row[2 * (k - 1) + 1], s)) : 0;
+    base[i] = make_longlong2(nr - sr, ni - si);
+    zero[i] = make_longlong2(0, 0);
+    atomicAdd(&s_sum, s);
+    atomicAdd(&s_bound, kk - 1);
+    if (!fin) atomicOr(&s_flags, 1);
+    if (fin && absum == 0.0) atomicOr(&s_flags, 2);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    BatchMat* mm = const_cast<BatchMat*>(a.mats) + m;
+    mm->sum_s = s_sum;
+    mm->flags = s_flags | (s_bound + k > 1000 ? 4 : 0);
+  }
+}
+
+// Sweep steps t in [0, 2^c) of the chunk starting at g0 of a K x K matrix
+// whose table starts at D; adds the terms to (accr, acci).
+template <int K>
+__device__ __forceinline__ void batch_sweep(const longlong2* __restrict__ D, int sum_s, int c, uint64_t g0,
+                                            bool active, dd& accr, dd& acci) {
+  const longlong2* base = D + (size_t)2 * (K > 1 ? K - 1 : 0) * K;
+  const longlong2* zero = base + K;
+  const int ebase = 62 * (K + 1) - 120 - sum_s - K;
+  const uint32_t nsteps = 1u << c;
+  const uint32_t kb = (uint32_t)((g0 >> c) & 1u) << c;
+  const uint32_t gpar = (uint32_t)(g0 & 1u);
+  long long Yr[K], Yi[K];
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    const longlong2 b = __ldg(base + i);
+    Yr[i] = b.x;
+    Yi[i] = b.y;
+  }
+  const uint64_t G = gray64(g0);
+  for (int j = (c > 0 ? c - 1 : 0); j < K - 1; ++j) {
+    const long long msk = -(long long)((G >> j) & 1u);
+    const longlong2* col = D + (size_t)(2 * j) * K;
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      const longlong2 d = __ldg(col + i);
+      Yr[i] += d.x & msk;
+      Yi[i] += d.y & msk;
+    }
+  }
+  for (uint32_t t = 0; t < nsteps; ++t) {
+    const int j = __ffs(t) - 1;
+    const uint32_t sb = ((t | kb) >> (j + 1)) & 1u;
+    const longlong2* col = t ? D + (size_t)(2 * j + sb) * K : zero;
+    CProd pa, pb;
+    cprod_init(pa);
+    cprod_init(pb);
+    int sa = 0, sbb = 0;
+#pragma unroll
+    for (int i = 0; i < K; i += 2) {
+      const longlong2 d0 = __ldg(col + i);
+      Yr[i] += d0.x;
+      Yi[i] += d0.y;
+      sa += cprod_mul(pa, Yr[i], Yi[i]);
+      if (i + 1 < K) {
+        const longlong2 d1 = __ldg(col + i + 1);
+        Yr[i + 1] += d1.x;
+        Yi[i + 1] += d1.y;
+        sbb += cprod_mul(pb, Yr[i + 1], Yi[i + 1]);
+      }
+    }
+    const long long br_ = ((long long)pb.r1 << 31) | pb.r0;
+    const long long bi_ = ((long long)pb.i1 << 31) | pb.i0;
+    const int sm = cprod_mul(pa, br_, bi_);
+    const long long zr = ((long long)pa.r1 << 31) | pa.r0;
+    const long long zi = ((long long)pa.i1 << 31) | pa.i0;
+    const int e = ebase - (sa + sbb + sm);
+    const double hr = (double)zr, hi_ = (double)zi;
+    const double lr = (double)(zr - __double2ll_rn(hr)), li = (double)(zi - __double2ll_rn(hi_));
+    const double sc = ldexp(((t ^ gpar) & 1u) ? -1.0 : 1.0, e);
+    dd_acc(accr, active ? hr * sc : 0.0, active ? lr * sc : 0.0);
+    dd_acc(acci, active ? hi_ * sc : 0.0, active ? li * sc : 0.0);
+  }
+  accr = dd_make(accr.hi, accr.lo);
+  acci = dd_make(acci.hi, acci.lo);
+}
+
+template <int K>
+__device__ __forceinline__ void batch_item(const BatchArgs& a, const BatchItem& it) {
+  const int lane = threadIdx.x & 31;
+  dd accr = {0.0, 0.0}, acci = {0.0, 0.0};
+  if (it.mode == kLaneMode) {
+    const bool active = lane < it.count;
+    const int m = a.lane_mats[it.mat + (active ? lane : 0)];
+    const BatchMat bm = a.mats[m];
+    const bool ok = active && bm.flags == 0;
+    batch_sweep<K>(a.table + bm.d_off, bm.sum_s, K - 1, 0ull, ok, accr, acci);
+    if (active) {
+      a.slots[2 * bm.slot0] = accr;
+      a.slots[2 * bm.slot0 + 1] = acci;
+    }
+  } else {
+    const BatchMat bm = a.mats[it.mat];
+    const uint64_t chunk = (uint64_t)it.chunk0 + lane;
+    const uint64_t nchunks = 1ull << (K - 1 - it.c);
+    const bool active = chunk < nchunks && bm.flags == 0;
+    batch_sweep<K>(a.table + bm.d_off, bm.sum_s, it.c, (active ? chunk : 0ull) << it.c, active, accr, acci);
+    accr = dd_warp_sum(accr);
+    acci = dd_warp_sum(acci);
+    if (lane == 0) {
+      a.slots[2 * it.slot] = accr;
+      a.slots[2 * it.slot + 1] = acci;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kBlock, 1) batch_main_kernel(BatchArgs a) {
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    int idx = 0;
+    if (lane == 0) idx = (int)atomicAdd(a.counter, 1u);
+    idx = __shfl_sync(0xffffffffu, idx, 0);
+    if (idx >= a.nitems) break;
+    const BatchItem it = a.items[idx];
+    switch (it.k) {
+#define PERM_BATCH_CASE(KK) \
+  case KK:                  \
+    batch_item<KK>(a, it);  \
+    break;
+      PERM_BATCH_CASE(1) PERM_BATCH_CASE(2) PERM_BATCH_CASE(3) PERM_BATCH_CASE(4) PERM_BATCH_CASE(5)
+      PERM_BATCH_CASE(6) PERM_BATCH_CASE(7) PERM_BATCH_CASE(8) PERM_BATCH_CASE(9) PERM_BATCH_CASE(10)
+      PERM_BATCH_CASE(11) PERM_BATCH_CASE(12) PERM_BATCH_CASE(13) PERM_BATCH_CASE(14) PERM_BATCH_CASE(15)
+      PERM_BATCH_CASE(16) PERM_BATCH_CASE(17) PERM_BATCH_CASE(18) PERM_BATCH_CASE(19) PERM_BATCH_CASE(20)
+      PERM_BATCH_CASE(21) PERM_BATCH_CASE(22) PERM_BATCH_CASE(23) PERM_BATCH_CASE(24) PERM_BATCH_CASE(25)
+      PERM_BATCH_CASE(26) PERM_BATCH_CASE(27) PERM_BATCH_CASE(28) PERM_BATCH_CASE(29) PERM_BATCH_CASE(30)
+      PERM_BATCH_CASE(31) PERM_BATCH_CASE(32)
+#undef PERM_BATCH_CASE
+      default:
+        break;
+    }
+  }
+}
+
+// One thread per matrix: its slots in order, then the factor 2 (-1)^(k-1).
+__global__ void batch_finish_kernel(BatchArgs a, const int32_t* nslots) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= a.nmats) return;
+  const BatchMat bm = a.mats[m];
+  dd r = {0.0, 0.0}, im = {0.0, 0.0};
+  for (int s = 0; s < nslots[m]; ++s) {
+    r = dd_add(r, a.slots[2 * (bm.slot0 + s)]);
+    im = dd_add(im, a.slots[2 * (bm.slot0 + s) + 1]);
+  }
+  const double f = (bm.k & 1) ? 2.0 : -2.0;
+  const double nan = __longlong_as_double(0x7ff8000000000000ll);
+  int32_t st = PERM_OK;
+  if (bm.flags & 1) st = PERM_EINVAL;
+  else if (bm.flags & 4) st = PERM_ERANGE;
+  if (st != PERM_OK) {
+    a.out[2 * m] = nan;
+    a.out[2 * m + 1] = nan;
+  } else if (bm.flags & 2) {
+    a.out[2 * m] = 0.0;
+    a.out[2 * m + 1] = 0.0;
+  } else {
+    a.out[2 * m] = (r.hi + r.lo) * f;
+    a.out[2 * m + 1] = (im.hi + im.lo) * f;
+  }
+  if (a.status) a.status[m] = st;
+}
+
+}  // namespace permgpu
+
+using namespace permgpu;
+
+struct perm_batch_plan {
+  int device = 0;
+  int count = 0;
+  int sms = 0;
+  int max_k = 0;
+  std::vector<int> ks;
+  std::vector<int64_t> a_off;
+  // per size class: mode and chunk exponent
+  int cls_mode[kBatchKMax + 1];
+  int cls_c[kBatchKMax + 1];
+  // device buffers (owned)
+  BatchMat* d_mats = nullptr;
+  BatchItem* d_items = nullptr;
+  int32_t* d_lane_mats = nullptr;
+  int32_t* d_nslots = nullptr;
+  longlong2* d_table = nullptr;
+  dd* d_slots = nullptr;
+  unsigned int* d_counter = nullptr;
+  int nitems = 0;
+  int nslots_total = 0;
+  size_t table_elems = 0;
+  // bound buffers and the captured graph
+  const double* A = nullptr;
+  double* out = nullptr;
+  int32_t* status = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph = nullptr;
+};
+
+static void batch_free(perm_batch_plan* p) {
+  if (!p) return;
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  cudaFree(p->d_mats);
+  cudaFree(p->d_items);
+  cudaFree(p->d_lane_mats);
+  cudaFree(p->d_nslots);
+  cudaFree(p->d_table);
+  cudaFree(p->d_slots);
+  cudaFree(p->d_counter);
+  delete p;
+}
+
+// Default choice per size class: one matrix per lane while a sweep is short,
+// otherwise chunks of 2^c steps with at least ~8 warp items per matrix.
+static void batch_default_classes(perm_batch_plan* p) {
+  for (int k = 0; k <= kBatchKMax; ++k) {
+    if (k <= 14) {
+      p->cls_mode[k] = kLaneMode;
+      p->cls_c[k] = k > 0 ? k - 1 : 0;
+    } else {
+      p->cls_mode[k] = kWarpMode;
+      int c = k - 1 - 5 - 3;  // 32 chunks per item, 8 items per matrix
+      if (c < 6) c = 6;
+      if (c > k - 1) c = k - 1;
+      p->cls_c[k] = c;
+    }
+  }
+}
+
+// Build the work queue, slots and matrix records for the current class
+// choices (host), and upload them.
+static int batch_build(perm_batch_plan* p) {
+  std::vector<BatchMat> mats(p->count);
+  std::vector<int32_t> nslots(p->count, 0);
+  std::vector<BatchItem> items;
+  std::vector<int32_t> lane_mats;
+  size_t toff = 0;
+  for (int m = 0; m < p->count; ++m) {
+    const int k = p->ks[m];
+    mats[m].k = k;
+    mats[m].sum_s = 0;
+    mats[m].flags = 0;
+    mats[m].a_off = p->a_off[m];
+    mats[m].d_off = (int64_t)toff;
+    toff += (size_t)2 * (k > 1 ? k - 1 : 0) * k + 2 * (size_t)k;
+  }
+  p->table_elems = toff;
+  // slots: lane-mode matrices one slot, warp-mode one per item
+  int slot = 0;
+  struct Cost {
+    double cost;
+    int idx;
+  };
+  std::vector<Cost> order;
+  for (int k = 1; k <= kBatchKMax; ++k) {
+    std::vector<int> ms;
+    for (int m = 0; m < p->count; ++m)
+      if (p->ks[m] == k) ms.push_back(m);
+    if (ms.empty()) continue;
+    if (p->cls_mode[k] == kLaneMode) {
+      for (size_t g = 0; g < ms.size(); g += 32) {
+        BatchItem it;
+        memset(&it, 0, sizeof(it));
+        it.mode = kLaneMode;
+        it.k = k;
+        it.c = k - 1;
+        it.count = (int)std::min<size_t>(32, ms.size() - g);
+        it.mat = (int)lane_mats.size();
+        for (int q = 0; q < it.count; ++q) {
+          const int m = ms[g + q];
+          lane_mats.push_back(m);
+          mats[m].slot0 = slot++;
+          nslots[m] = 1;
+        }
+        items.push_back(it);
+      }
+    } else {
+      const int c = p->cls_c[k];
+      const uint64_t nchunks = 1ull << (k - 1 - c);
+      for (int m : ms) {
+        mats[m].slot0 = slot;
+        for (uint64_t ch = 0; ch < nchunks; ch += 32) {
+          BatchItem it;
+          memset(&it, 0, sizeof(it));
+          it.mode = kWarpMode;
+          it.k = k;
+          it.c = c;
+          it.count = 32;
+          it.mat = m;
+          it.slot = slot++;
+          it.chunk0 = (int64_t)ch;
+          items.push_back(it);
+          nslots[m]++;
+        }
+      }
+    }
+  }
+  // longest first: cost ~ steps x k per item
+  std::vector<size_t> idx(items.size());
+  for (size_t i = 0; i < idx.size(); ++i) idx[i] = i;
+  auto cost = [&](const BatchItem& it) {
+    double steps = it.mode == kLaneMode ? (double)(1ull << (it.k - 1)) : (double)(1ull << it.c);
+    return steps * (it.k + 4);
+  };
+  std::stable_sort(idx.begin(), idx.end(), [&](size_t x, size_t y) { return cost(items[x]) > cost(items[y]); });
+  std::vector<BatchItem> sorted(items.size());
+  for (size_t i = 0; i < idx.size(); ++i) sorted[i] = items[idx[i]];
+  p->nitems = (int)sorted.size();
+  p->nslots_total = slot;
+
+  cudaFree(p->d_mats);
+  cudaFree(p->d_items);
+  cudaFree(p->d_lane_mats);
+  cudaFree(p->d_nslots);
+  cudaFree(p->d_table);
+  cudaFree(p->d_slots);
+  p->d_mats = nullptr;
+  p->d_items = nullptr;
+  p->d_lane_mats = nullptr;
+  p->d_nslots = nullptr;
+  p->d_table = nullptr;
+  p->d_slots = nullptr;
+  if (cudaMalloc(&p->d_mats, sizeof(BatchMat) * std::max(1, p->count)) != cudaSuccess ||
+      cudaMalloc(&p->d_items, sizeof(BatchItem) * std::max(1, p->nitems)) != cudaSuccess ||
+      cudaMalloc(&p->d_lane_mats, sizeof(int32_t) * std::max<size_t>(1, lane_mats.size())) != cudaSuccess ||
+      cudaMalloc(&p->d_nslots, sizeof(int32_t) * std::max(1, p->count)) != cudaSuccess ||
+      cudaMalloc(&p->d_table, sizeof(longlong2) * std::max<size_t>(1, p->table_elems)) != cudaSuccess ||
+      cudaMalloc(&p->d_slots, sizeof(dd) * 2 * std::max(1, p->nslots_total)) != cudaSuccess) {
+    cudaGetLastError();
+    return PERM_ENOMEM;
+  }
+  if (!p->d_counter && cudaMalloc(&p->d_counter, sizeof(unsigned int)) != cudaSuccess) {
+    cudaGetLastError();
+    return PERM_ENOMEM;
+  }
+  if (cudaMemcpy(p->d_mats, mats.data(), sizeof(BatchMat) * p->count, cudaMemcpyHostToDevice) != cudaSuccess ||
+      (p->nitems && cudaMemcpy(p->d_items, sorted.data(), sizeof(BatchItem) * p->nitems, cudaMemcpyHostToDevice) !=
+                        cudaSuccess) ||
+      (!lane_mats.empty() && cudaMemcpy(p->d_lane_mats, lane_mats.data(), sizeof(int32_t) * lane_mats.size(),
+                                        cudaMemcpyHostToDevice) != cudaSuccess) ||
+      cudaMemcpy(p->d_nslots, nslots.data(), sizeof(int32_t) * p->count, cudaMemcpyHostToDevice) != cudaSuccess)
+    return PERM_ECUDA;
+  return PERM_OK;
+}
+
+static BatchArgs batch_args(const perm_batch_plan* p) {
+  BatchArgs a;
+  memset(&a, 0, sizeof(a));
+  a.A = p->A;
+  a.mats = p->d_mats;
+  a.items = p->d_items;
+  a.lane_mats = p->d_lane_mats;
+  a.table = p->d_table;
+  a.slots = p->d_slots;
+  a.counter = p->d_counter;
+  a.out = p->out;
+  a.status = p->status;
+  a.nmats = p->count;
+  a.nitems = p->nitems;
+  return a;
+}
+
+// The execution sequence (captured into the plan's graph).
+static int batch_enqueue(const perm_batch_plan* p, cudaStream_t s) {
+  BatchArgs a = batch_args(p);
+  if (cudaMemsetAsync(p->d_counter, 0, sizeof(unsigned int), s) != cudaSuccess) return PERM_ECUDA;
+  batch_prep_kernel<<<p->count, kBlock, 0, s>>>(a);
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_main_kernel, kBlock, 0) != cudaSuccess || nb < 1)
+    nb = 1;
+  int want = (p->nitems + kWarps - 1) / kWarps;
+  int grid = std::max(1, std::min(p->sms * nb, want));
+  batch_main_kernel<<<grid, kBlock, 0, s>>>(a);
+  batch_finish_kernel<<<(p->count + 127) / 128, 128, 0, s>>>(a, p->d_nslots);
+  return cudaGetLastError() == cudaSuccess ? PERM_OK : PERM_ECUDA;
+}
+
+static int batch_capture(perm_batch_plan* p) {
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  p->exec = nullptr;
+  p->graph = nullptr;
+  cudaStream_t cs;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return PERM_ECUDA;
+  int rc = PERM_OK;
+  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) rc = PERM_ECUDA;
+  if (!rc) rc = batch_enqueue(p, cs);
+  cudaGraph_t g = nullptr;
+  if (cudaStreamEndCapture(cs, &g) != cudaSuccess) rc = PERM_ECUDA;
+  if (!rc && cudaGraphInstantiate(&p->exec, g, 0) != cudaSuccess) rc = PERM_ECUDA;
+  p->graph = g;
+  cudaStreamDestroy(cs);
+  if (rc) cudaGetLastError();
+  return rc;
+}
+
+extern "C" int perm_batched_plan_create(perm_batch_plan** plan, int type, const int* ns_host, int count,
+                                        const void* A_packed, const int64_t* offsets_host, void* out,
+                                        int32_t* status) {
+  if (!plan) return PERM_EINVAL;
+  *plan = nullptr;
+  if (type != PERM_C128) return PERM_EINVAL;
+  if (count < 1 || !ns_host || !offsets_host || !A_packed || !out) return PERM_EINVAL;
+  perm_batch_plan* p = new perm_batch_plan();
+  if (cudaGetDevice(&p->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) {
+    delete p;
+    return PERM_ECUDA;
+  }
+  p->count = count;
+  p->ks.assign(ns_host, ns_host + count);
+  p->a_off.assign(offsets_host, offsets_host + count);
+  for (int k : p->ks) {
+    if (k < 1 || k > kBatchKMax) {
+      delete p;
+      return PERM_ERANGE;
+    }
+    p->max_k = std::max(p->max_k, k);
+  }
+  for (int64_t o : p->a_off)
+    if (o < 0) {
+      delete p;
+      return PERM_EINVAL;
+    }
+  p->A = static_cast<const double*>(A_packed);
+  p->out = static_cast<double*>(out);
+  p->status = status;
+  batch_default_classes(p);
+  int rc = batch_build(p);
+  if (!rc) rc = batch_capture(p);
+  if (rc) {
+    batch_free(p);
+    return rc;
+  }
+  *plan = p;
+  return PERM_OK;
+}
+
+extern "C" int perm_batched(perm_batch_plan* plan, void* stream) {
+  if (!plan || !plan->exec) return PERM_EINVAL;
+  return cudaGraphLaunch(plan->exec, static_cast<cudaStream_t>(stream)) == cudaSuccess ? PERM_OK : PERM_ECUDA;
+}
+
+extern "C" int perm_batched_autotune(perm_batch_plan* plan, int rounds, void* stream) {
+  if (!plan) return PERM_EINVAL;
+  if (rounds < 1) rounds = 1;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return PERM_ECUDA;
+  // tune one size class at a time: plans that hold only that class's matrices
+  int rc = PERM_OK;
+  for (int k = 1; k <= kBatchKMax && !rc; ++k) {
+    std::vector<int> ks;
+    std::vector<int64_t> offs;
+    for (int m = 0; m < plan->count; ++m)
+      if (plan->ks[m] == k) {
+        ks.push_back(k);
+        offs.push_back(plan->a_off[m]);
+      }
+    if (ks.empty()) continue;
+    struct Cand {
+      int mode, c;
+    };
+    std::vector<Cand> cands;
+    if (k <= 16) cands.push_back({kLaneMode, k - 1});
+    for (int c = std::max(2, k - 1 - 12); c <= k - 1 - 5; ++c) cands.push_back({kWarpMode, c});
+    if (cands.empty()) cands.push_back({kLaneMode, k - 1});
+    float best = 1e30f;
+    Cand pick = {plan->cls_mode[k], plan->cls_c[k]};
+    for (const Cand& cd : cands) {
+      perm_batch_plan* q = new perm_batch_plan();
+      q->device = plan->device;
+      q->sms = plan->sms;
+      q->count = (int)ks.size();
+      q->ks = ks;
+      q->a_off = offs;
+      q->max_k = k;
+      q->A = plan->A;
+      q->out = plan->out;  // scratch use of the caller's output (rewritten below)
+      q->status = nullptr;
+      batch_default_classes(q);
+      q->cls_mode[k] = cd.mode;
+      q->cls_c[k] = cd.c;
+      int r = batch_build(q);
+      float ms = 1e30f;
+      if (!r) {
+        batch_enqueue(q, s);  // warm-up
+        cudaEventRecord(e0, s);
+        for (int it = 0; it < rounds; ++it) batch_enqueue(q, s);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+      }
+      batch_free(q);
+      if (ms < best) {
+        best = ms;
+        pick = cd;
+      }
+    }
+    plan->cls_mode[k] = pick.mode;
+    plan->cls_c[k] = pick.c;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (!rc) rc = batch_build(plan);
+  if (!rc) rc = batch_capture(plan);
+  return rc;
+}
+
+extern "C" int perm_batched_plan_info(const perm_batch_plan* plan, int k, int* mode, int* c, int* nitems) {
+  if (!plan || k < 0 || k > kBatchKMax) return PERM_EINVAL;
+  if (mode) *mode = plan->cls_mode[k];
+  if (c) *c = plan->cls_c[k];
+  if (nitems) *nitems = plan->nitems;
+  return PERM_OK;
+}
+
+extern "C" void perm_batched_plan_destroy(perm_batch_plan* plan) { batch_free(plan); }

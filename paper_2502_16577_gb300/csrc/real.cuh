@@ -39,8 +39,9 @@ __device__ __forceinline__ void prod_init(Prod& p) {
   p.m1 = 1u << 30;  // 2^62
 }
 
-// p <- p * A for A = a1:a0 < 2^63: v = floor(M A / 2^64) up to one unit (the
-// partial product m0*a0 is dropped and +1 unit is added back on average),
+// p <- p * A for A = a1:a0 < 2^63: v = M A / 2^64 rounded to nearest up to
+// the dropped partial product m0*a0 (< 1 unit; +1/2 unit is added to the
+// middle partial products, so products of integers that fit stay exact),
 // then M <- v << (30 - pos) with pos the index of the top set bit of v_hi, so
 // that M is back in [2^62, 2^63).  Returns pos (-1 if v_hi is zero, when the
 // shift is 31).  The multiply-adds issue on the IMAD pipe and the shifts on the
@@ -52,7 +53,7 @@ __device__ __forceinline__ uint32_t prod_mul(Prod& p, uint32_t a0, uint32_t a1) 
   asm("{\n\t"
       ".reg .u64 t, u;\n\t"
       ".reg .u32 ul, uh, vl, vh, s;\n\t"
-      "mad.wide.u32 t, %2, %3, 4294967296;\n\t"
+      "mad.wide.u32 t, %2, %3, 2147483648;\n\t"
       "mad.wide.u32 u, %1, %4, t;\n\t"
       "mov.b64 {ul, uh}, u;\n\t"
       "mad.lo.cc.u32 vl, %2, %4, uh;\n\t"
