@@ -307,6 +307,9 @@ def run_gpu(args):
     if rank != 0:
         return 0
 
+    batched = None if args.no_batched else measure_batched(pg, dev, stream)
+    grad = None if args.no_batched else measure_grad(pg, dev, stream)
+
     # roofline of the dominant kernel (dense real n=40): issue-slot work of the
     # integer factor sequence against the SM issue peak; FP64 view alongside
     n40 = 40
@@ -344,6 +347,8 @@ def run_gpu(args):
                       "paper_gv100_steps_per_s": 2 ** 39 / 14.17},
         "pipe_peaks": peaks,
         "per_config_ms": {"real40": statistics.mean(real_ms)},
+        "batched": batched,
+        "grad": grad,
         "clocks": clocks,
         "e2e": e2e,
     }
@@ -356,6 +361,153 @@ def run_gpu(args):
     return 0
 
 
+def measure_batched(pg, dev, stream, count: int = 8192):
+    """Batched boson workload: 8192 complex k x k submatrices (k uniform in
+    8..26, rows with replacement from a Haar 256 x 256 unitary): one graph
+    replay of the batched plan vs a loop of perm() launches on one stream."""
+    import torch
+
+    mats = syn.batched_boson(count)
+    plan = pg.BatchPlan(mats, device=dev)
+    plan.run(stream)  # warm-up
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    e0, e1 = ev(), ev()
+    e0.record(stream)
+    plan.run_async(stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    t_graph = e0.elapsed_time(e1) * 1e-3
+    res = plan.run(stream)
+    devm = [torch.from_numpy(np.ascontiguousarray(m)).to(dev) for m in mats]
+    out = torch.zeros(2 * count, dtype=torch.float64, device=dev)
+    st = torch.zeros(count, dtype=torch.int32, device=dev)
+    for i in range(64):
+        pg.perm_async(devm[i], out[2 * i:2 * i + 2], st[i:i + 1], stream)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for i in range(count):
+        pg.perm_async(devm[i], out[2 * i:2 * i + 2], st[i:i + 1], stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    t_loop = e0.elapsed_time(e1) * 1e-3
+    o = out.cpu().numpy()
+    same = bool(np.array_equal(res, o[0::2] + 1j * o[1::2]))
+    plan.close()
+    steps = sum(1 << (m.shape[0] - 1) for m in mats)
+    return {"workload": f"{count} complex128 boson submatrices, k uniform 8..26", "perms_per_s": count / t_graph,
+            "steps_per_s": steps / t_graph, "loop_perms_per_s": count / t_loop, "speedup_vs_loop": t_loop / t_graph,
+            "identical_to_loop": same, "launches_per_replay": 3}
+
+
+def measure_grad(pg, dev, stream, reps: int = 3):
+    """Fused gradient: dense real n=28 uniform [-1, 1) (perm_grad vs perm on the
+    same matrix, and vs n^2 forwards of one (n-1) minor), and 1024 complex
+    16 x 16 Haar submatrices (perm_grad_batched vs the batched forward plan)."""
+    import torch
+
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize(dev)
+        ts = []
+        for _ in range(reps):
+            e0, e1 = ev(), ev()
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ts.append(e0.elapsed_time(e1) * 1e-3)
+        return statistics.median(ts)
+
+    A = torch.from_numpy(syn.grad_real_28()).to(dev)
+    n = A.shape[0]
+    out = torch.zeros(2, dtype=torch.float64, device=dev)
+    G = torch.empty_like(A)
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    t_grad = timed(lambda: pg.perm_grad_async(A, out[:1], G, st, stream))
+    t_fwd = timed(lambda: pg.perm_async(A, out, st, stream))
+    M = A[1:, 1:].contiguous()
+    t_minor = timed(lambda: pg.perm_async(M, out, st, stream))
+    mats = syn.grad_boson_16(1024)
+    B = torch.from_numpy(mats).to(dev)
+    bout = torch.zeros(1024, dtype=torch.complex128, device=dev)
+    BG = torch.empty_like(B)
+    t_bgrad = timed(lambda: pg.perm_grad_batched_async(B, bout, BG, st, stream))
+    plan = pg.BatchPlan(list(mats), device=dev)
+    t_bfwd = timed(lambda: plan.run_async(stream))
+    plan.close()
+    k = mats.shape[1]
+    return {"real28": {"grad_ms": t_grad * 1e3, "fwd_ms": t_fwd * 1e3, "grad_over_fwd": t_grad / t_fwd,
+                       "steps_per_s": (1 << (n - 1)) / t_grad,
+                       "n2_minor_forwards_ms": n * n * t_minor * 1e3,
+                       "speedup_vs_n2_minor_forwards": n * n * t_minor / t_grad},
+            "complex16_x1024": {"grad_ms": t_bgrad * 1e3, "fwd_ms": t_bfwd * 1e3,
+                                "grad_over_fwd": t_bgrad / t_bfwd,
+                                "steps_per_s": 1024 * (1 << (k - 1)) / t_bgrad},
+            "launches": "grad: 1 sweep + 3 small finishing kernels; fwd: 1 (real), 3 per graph replay (batched)"}
+
+
+def run_case(args):
+    """One kernel on one input, for profiling and sweeps: KIND:N with KIND in
+    real (uniform [-1, 1)), bin (Bernoulli 0.5), cplx (Haar unitary), sparse
+    (density 0.2, CCS), grad (real, fused gradient), bgrad (1024 complex N x N
+    boson submatrices, batched gradient).  Prints one JSON line."""
+    import torch
+
+    import paper_2502_16577_gb300 as pg
+
+    pg.load()
+    kind, n = args.case.split(":")
+    n = int(n)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    seed = syn.SEED_BASE + 100 + n
+    steps = 1 << (n - 1)
+    if kind in ("real", "bin", "cplx"):
+        A = {"real": lambda: syn.signed_real(n, seed), "bin": lambda: syn.bernoulli01(n, seed),
+             "cplx": lambda: syn.haar_unitary(n, seed)}[kind]()
+        A = torch.from_numpy(A).to(dev)
+        out = torch.zeros(4, dtype=torch.int64 if kind == "bin" else torch.float64, device=dev)
+        fn = lambda: pg.perm_async(A, out, st, stream)
+    elif kind == "sparse":
+        cp, ri, cv = syn.to_ccs(syn.sparse_real(n, seed, 0.2))
+        cp, ri, cv = (torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in (cp, ri, cv))
+        out = torch.zeros(1, dtype=torch.float64, device=dev)
+        fn = lambda: pg.perm_sparse_async(n, cp, ri, cv, out, st, stream)
+    elif kind == "grad":
+        A = torch.from_numpy(syn.signed_real(n, seed)).to(dev)
+        out = torch.zeros(1, dtype=torch.float64, device=dev)
+        G = torch.empty_like(A)
+        fn = lambda: pg.perm_grad_async(A, out, G, st, stream)
+    elif kind == "bgrad":
+        B = torch.from_numpy(np.stack(syn.boson_submatrices(1024, seed, n, n, 256))).to(dev)
+        out = torch.zeros(1024, dtype=torch.complex128, device=dev)
+        G = torch.empty_like(B)
+        fn = lambda: pg.perm_grad_batched_async(B, out, G, st, stream)
+        steps *= 1024
+    else:
+        raise SystemExit(f"unknown case {args.case}")
+    for _ in range(args.warmup):
+        fn()
+    torch.cuda.synchronize(dev)
+    ms = []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms.append(e0.elapsed_time(e1))
+    if int(st.item()) != 0:
+        raise SystemExit(f"status {int(st.item())}")
+    t = statistics.median(ms)
+    print(json.dumps({"case": args.case, "ms": t, "steps_per_s": steps / (t * 1e-3), "launches": args.steps}),
+          flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -363,9 +515,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per launch of the dominant kernel from an ncu capture")
+    ap.add_argument("--case", default=None, help="KIND:N, one kernel on one input (profiling)")
     args = ap.parse_args()
+    if args.case:
+        return run_case(args)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
     if args.impl == "reference":

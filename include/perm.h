@@ -169,6 +169,74 @@ int perm_batched_plan_info(const perm_batch_plan* plan, int k, int* mode, int* c
 void perm_batched_plan_destroy(perm_batch_plan* plan);
 
 /*
+ * perm_grad - perm(A) and its full gradient G = d perm(A) / dA in one
+ * Gray-code sweep: G_kl = perm of A without row k and column l.
+ * Differentiating Eq. nwx (x_i = (1/2) sum_l delta_l a_il) gives
+ *   G_kl = (-1)^(n-1) sum_g (-1)^g delta_l(g) prod_{i != k} x_i(g),
+ * accumulated with per-chunk running prefixes so each step costs O(n)
+ * additions.  The paper has no gradient; the sweep and its chunking are those
+ * of Alg. 1 / Alg. 3.  The permanent is returned through the row expansion
+ * perm = sum_l a_0l G_0l (its error follows G's, not perm()'s).
+ *   type    PERM_F64 or PERM_C128 (interleaved re, im); 0 <= n <= 32.
+ *   A       device, n*n elements row-major;  out device, one element;
+ *   G       device, n*n elements row-major (the holomorphic derivative for
+ *           complex A: the gradient of a real loss L is conj(G) dL/dperm);
+ *   status  optional device int32: PERM_EINVAL for a non-finite entry (out and
+ *           G then NaN), PERM_ERANGE when the result would leave binary64.
+ * Allocates a workspace with cudaMallocAsync on `stream`; stream-ordered.
+ * Returns PERM_EINVAL / PERM_ERANGE for bad arguments before any launch.
+ */
+int perm_grad(const void* A, int n, int type, void* out, void* G, int32_t* status, void* stream);
+
+/*
+ * perm_grad_batched - perm_grad of `count` matrices of one order n, packed
+ * back to back (matrix p at A + p*n*n elements; out[p]; G at G + p*n*n).
+ * One sweep launch covers the whole batch (chunks of every matrix share the
+ * grid), then one finishing launch; status is the worst over the batch.
+ */
+int perm_grad_batched(const void* A, int n, int count, int type, void* out, void* G, int32_t* status,
+                      void* stream);
+
+/*
+ * Sparse preprocessing (Sec. 4; host-side graph work, leaves on the GPU).
+ *
+ * perm_decomp_create builds, from a HOST CCS matrix (same validation as
+ * perm_sparse; entries must be finite), the decomposition of Sec. 4:
+ *  - Dulmage-Mendelsohn (Sec. 4.1): entries that lie on no perfect matching
+ *    are removed; the rest is block-diagonal up to permutation, one block per
+ *    strongly connected component of the matched row/column graph, and
+ *    perm(A) = prod over blocks of perm(block).  No perfect matching:
+ *    structurally_zero = 1 and perm = 0.
+ *  - Forbert-Marx (Sec. 4.2, Eq. expand, Alg. 4): inside a block, rows or
+ *    columns with at most four nonzeros are expanded away; every block becomes
+ *    a sum of coefficient * perm(leaf).  At most max_leaves leaves are made
+ *    (<= 0: 4096); past that, the current matrix is kept as a leaf
+ *    (truncated = 1).
+ * perm_decomp_eval computes every leaf of order >= 2 on the GPU (dense kernel
+ * at density >= 30 %, sparse kernel otherwise) on `stream`, waits for them,
+ * and writes perm(A) to the HOST double *out.  Blocking.
+ * perm_sparse_decomp = create + eval + destroy (info optional).
+ * Ownership: the handle owns its matrices; leaf / filtered copy out to
+ * caller-owned host buffers (n*n doubles).
+ */
+typedef struct perm_decomp perm_decomp;
+typedef struct {
+  int n, nblocks, nleaves, max_leaf_n, structurally_zero, truncated;
+  int64_t removed_nnz;  /* entries removed by the Dulmage-Mendelsohn step */
+  double leaf_steps;    /* sum over leaves of order k >= 1 of 2^(k-1) */
+  double plain_steps;   /* 2^(n-1): the sweep without preprocessing */
+} perm_decomp_info_t;
+int perm_decomp_create(perm_decomp** d, int n, const int32_t* cptrs, const int32_t* rids, const double* cvals,
+                       int64_t nnz, int max_leaves);
+int perm_decomp_info(const perm_decomp* d, perm_decomp_info_t* info);
+int perm_decomp_leaf(const perm_decomp* d, int index, int* n, int* block, double* coef, double* A);
+int perm_decomp_filtered(const perm_decomp* d, double* A);
+int perm_decomp_eval(perm_decomp* d, double* out, void* stream);
+void perm_decomp_destroy(perm_decomp* d);
+int perm_sparse_decomp(int n, const int32_t* cptrs, const int32_t* rids, const double* cvals, int64_t nnz,
+                       double* out, perm_decomp_info_t* info, void* stream);
+
+/*
  * perm_host - perm() on host buffers: copies A in, runs perm() on stream,
  * copies the result out and waits.  Returns the device status as well.
  *   A_host   host, layout as perm()'s A;  out_host  host, layout as perm()'s out.

@@ -21,7 +21,7 @@ import numpy as np
 from . import _lib
 from ._lib import PERM_BIN, PERM_C128, PERM_F64, PermError, check, load
 
-__all__ = ["perm", "perm_async", "perm_range", "perm_range_async", "perm_combine", "perm_sparse", "perm_sparse_async", "perm_host", "pipe_peaks", "BatchPlan", "perm_type_of", "PermError",
+__all__ = ["perm", "perm_async", "perm_range", "perm_range_async", "perm_combine", "perm_sparse", "perm_sparse_async", "perm_host", "pipe_peaks", "BatchPlan", "perm_grad", "perm_grad_async", "perm_grad_batched", "perm_grad_batched_async", "permanent", "perm_type_of", "PermError",
            "PERM_F64", "PERM_C128", "PERM_BIN", "load"]
 
 
@@ -191,6 +191,125 @@ def perm_sparse(n: int, cptrs, rids, cvals, stream=None) -> float:
     s.synchronize()
     check(int(status.item()), "perm_sparse")
     return float(out.item())
+
+
+def _grad_type(A) -> int:
+    t = perm_type_of(A.dtype)
+    if t == PERM_BIN:
+        raise TypeError("perm_grad takes float64 or complex128 matrices")
+    return t
+
+
+def perm_grad_async(A, out, G, status=None, stream=None) -> None:
+    """Enqueue the fused permanent + gradient of an n x n CUDA tensor (float64
+    or complex128, n <= 32): out has one element of A's dtype, G is n x n."""
+    lib = load()
+    A = _as_device_matrix(A)
+    t = _grad_type(A)
+    h, _ = _stream_handle(stream)
+    rc = lib.perm_grad(ctypes.c_void_p(A.data_ptr()), A.shape[0], t, ctypes.c_void_p(out.data_ptr()),
+                       ctypes.c_void_p(G.data_ptr()), ctypes.c_void_p(status.data_ptr() if status is not None else 0),
+                       h)
+    check(rc, "perm_grad")
+
+
+def perm_grad(A, stream=None):
+    """(perm(A), d perm / dA) for a CUDA tensor; the permanent as a Python number,
+    the gradient as a tensor on A's device (holomorphic derivative for complex A)."""
+    torch = _torch()
+    A = _as_device_matrix(A)
+    out = torch.zeros(1, dtype=A.dtype, device=A.device)
+    G = torch.empty_like(A)
+    status = torch.full((1,), -1, dtype=torch.int32, device=A.device)
+    perm_grad_async(A, out, G, status, stream)
+    _, s = _stream_handle(stream)
+    s.synchronize()
+    check(int(status.item()), "perm_grad")
+    v = out.item()
+    return v, G
+
+
+def perm_grad_batched_async(A, out, G, status=None, stream=None) -> None:
+    """Enqueue perm_grad_batched over a (count, n, n) CUDA tensor."""
+    lib = load()
+    torch = _torch()
+    if not isinstance(A, torch.Tensor) or not A.is_cuda or A.dim() != 3 or A.shape[1] != A.shape[2]:
+        raise ValueError("A must be a CUDA tensor of shape (count, n, n)")
+    A = A.contiguous()
+    t = _grad_type(A)
+    h, _ = _stream_handle(stream)
+    rc = lib.perm_grad_batched(ctypes.c_void_p(A.data_ptr()), A.shape[1], A.shape[0], t,
+                               ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(G.data_ptr()),
+                               ctypes.c_void_p(status.data_ptr() if status is not None else 0), h)
+    check(rc, "perm_grad_batched")
+
+
+def perm_grad_batched(A, stream=None):
+    """(perms, grads) of a (count, n, n) CUDA tensor: perms (count,), grads (count, n, n)."""
+    torch = _torch()
+    A = A.contiguous()
+    out = torch.zeros(A.shape[0], dtype=A.dtype, device=A.device)
+    G = torch.empty_like(A)
+    status = torch.full((1,), -1, dtype=torch.int32, device=A.device)
+    perm_grad_batched_async(A, out, G, status, stream)
+    _, s = _stream_handle(stream)
+    s.synchronize()
+    check(int(status.item()), "perm_grad_batched")
+    return out, G
+
+
+def _autograd_function():
+    torch = _torch()
+
+    class Permanent(torch.autograd.Function):
+        """perm of a float64 / complex128 CUDA matrix (n, n) or batch (count, n, n).
+
+        A single matrix runs perm() forward and the fused gradient sweep
+        (perm_grad) backward; a batch runs perm_grad_batched once forward and
+        keeps G for backward.  For complex inputs backward returns
+        grad_out * conj(G), PyTorch's convention for holomorphic functions."""
+
+        @staticmethod
+        def forward(ctx, A):
+            if A.dim() == 3:
+                out, G = perm_grad_batched(A)
+                ctx.save_for_backward(G)
+                ctx.batched = True
+                return out
+            A = _as_device_matrix(A)
+            out, status = _out_buffers(perm_type_of(A.dtype), A.device, 2 if A.is_complex() else 1)
+            perm_async(A, out, status)
+            torch.cuda.current_stream().synchronize()
+            check(int(status.item()), "perm")
+            ctx.save_for_backward(A)
+            ctx.batched = False
+            v = torch.view_as_complex(out.view(1, 2))[0] if A.is_complex() else out[0]
+            return v.clone()
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            (X,) = ctx.saved_tensors
+            if ctx.batched:
+                G = X
+                g = grad_out.reshape(-1, 1, 1)
+            else:
+                _, G = perm_grad(X)
+                g = grad_out
+            return g * (G.conj() if G.is_complex() else G)
+
+    return Permanent
+
+
+_PERMANENT = None
+
+
+def permanent(A):
+    """Differentiable permanent (torch.autograd) of a float64 / complex128 CUDA
+    matrix (n, n) -> scalar, or of a batch (count, n, n) -> (count,)."""
+    global _PERMANENT
+    if _PERMANENT is None:
+        _PERMANENT = _autograd_function()
+    return _PERMANENT.apply(A)
 
 
 class BatchPlan:

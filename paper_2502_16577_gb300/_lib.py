@@ -19,7 +19,16 @@ _lib = None
 
 SYMBOLS = ("perm", "perm_range", "perm_combine", "perm_sparse", "perm_host", "perm_pipe_peaks",
            "perm_batched_plan_create", "perm_batched", "perm_batched_autotune", "perm_batched_plan_info",
-           "perm_batched_plan_destroy", "perm_status_string", "perm_abi_version")
+           "perm_batched_plan_destroy", "perm_grad", "perm_grad_batched", "perm_decomp_create", "perm_decomp_info", "perm_decomp_leaf",
+           "perm_decomp_filtered", "perm_decomp_eval", "perm_decomp_destroy", "perm_sparse_decomp",
+           "perm_status_string", "perm_abi_version")
+
+
+class DecompInfo(ctypes.Structure):
+    """perm_decomp_info_t of include/perm.h."""
+    _fields_ = [("n", ctypes.c_int), ("nblocks", ctypes.c_int), ("nleaves", ctypes.c_int),
+                ("max_leaf_n", ctypes.c_int), ("structurally_zero", ctypes.c_int), ("truncated", ctypes.c_int),
+                ("removed_nnz", ctypes.c_int64), ("leaf_steps", ctypes.c_double), ("plain_steps", ctypes.c_double)]
 
 
 class PermError(RuntimeError):
@@ -63,6 +72,27 @@ def load(build_if_missing: bool = False):
                                            ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     lib.perm_batched_plan_destroy.restype = None
     lib.perm_batched_plan_destroy.argtypes = [_vp]
+    lib.perm_grad.restype = ctypes.c_int
+    lib.perm_grad.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp]
+    lib.perm_grad_batched.restype = ctypes.c_int
+    lib.perm_grad_batched.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp]
+    _dp = ctypes.POINTER(ctypes.c_double)
+    _ip = ctypes.POINTER(ctypes.c_int)
+    lib.perm_decomp_create.restype = ctypes.c_int
+    lib.perm_decomp_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, _vp, _vp, _vp, ctypes.c_int64, ctypes.c_int]
+    lib.perm_decomp_info.restype = ctypes.c_int
+    lib.perm_decomp_info.argtypes = [_vp, ctypes.POINTER(DecompInfo)]
+    lib.perm_decomp_leaf.restype = ctypes.c_int
+    lib.perm_decomp_leaf.argtypes = [_vp, ctypes.c_int, _ip, _ip, _dp, _vp]
+    lib.perm_decomp_filtered.restype = ctypes.c_int
+    lib.perm_decomp_filtered.argtypes = [_vp, _vp]
+    lib.perm_decomp_eval.restype = ctypes.c_int
+    lib.perm_decomp_eval.argtypes = [_vp, _dp, _vp]
+    lib.perm_decomp_destroy.restype = None
+    lib.perm_decomp_destroy.argtypes = [_vp]
+    lib.perm_sparse_decomp.restype = ctypes.c_int
+    lib.perm_sparse_decomp.argtypes = [ctypes.c_int, _vp, _vp, _vp, ctypes.c_int64, _dp, ctypes.POINTER(DecompInfo),
+                                       _vp]
     lib.perm_host.restype = ctypes.c_int
     lib.perm_host.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp]
     lib.perm_pipe_peaks.restype = ctypes.c_int

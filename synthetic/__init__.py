@@ -222,3 +222,14 @@ def sparse_44():
 
 def batched_boson(count: int = 8192):
     return boson_submatrices(count, SEED_BASE + 6, 8, 26, 256)
+
+
+def grad_real_28():
+    """Gradient workload: dense real n=28, uniform [-1, 1)."""
+    return signed_real(28, SEED_BASE + 7)
+
+
+def grad_boson_16(count: int = 1024) -> np.ndarray:
+    """Gradient workload: count complex 16 x 16 boson-sampling submatrices of a
+    Haar 256 x 256 unitary (rows with replacement, first 16 columns), stacked."""
+    return np.stack(boson_submatrices(count, SEED_BASE + 8, 16, 16, 256))

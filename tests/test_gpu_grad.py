@@ -1,0 +1,263 @@
+"""The fused gradient (perm_grad / perm_grad_batched through the C ABI) on a
+GB300: against the oracle's minor permanents, closed forms, exact central
+differences of the oracle (perm is affine in every entry), the row-expansion
+identity and torch.autograd.gradcheck.
+
+Tolerance of G_kl (besides the 1e-10 perm(|minor|) bar): every term
+v_k(g) = prod_{i != k} x_i(g) carries a relative error below 2^-52 (62-bit
+products, one rounding to binary64); the terms are summed in binary64 in
+chunks of at most 2^9 steps, then over 16 chunks, then over at most a few
+hundred block-items per CTA, then in double-double.  The recursive-summation
+bound is then below (2^9 + 16 + 512 + 2) 2^-53 S_k < 2^-42 S_k with
+S_k = sum_g |v_k(g)|, so 2^-40 S_k holds with margin; S_k is computed here
+exactly enough in numpy for n <= 16."""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+import synthetic as syn
+
+pytestmark = pytest.mark.gpu
+
+TOL_S = 2.0 ** -40
+
+
+@pytest.fixture(scope="module")
+def pg():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2502_16577_gb300 as pg
+    from paper_2502_16577_gb300 import build
+
+    build.build()
+    pg.load()
+    return pg
+
+
+def _dev(A):
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(A)).cuda()
+
+
+def _minor(A, k, l):
+    return np.delete(np.delete(A, k, 0), l, 1)
+
+
+def _abs_scale(A):
+    """S_k = sum over the 2^(n-1) Gray subsets of prod_{i != k} |x_i| (n <= 16)."""
+    n = A.shape[0]
+    if n == 1:
+        return np.ones(1)
+    signs = np.array(list(itertools.product((-1.0, 1.0), repeat=n - 1)))
+    D = np.concatenate([signs, np.ones((signs.shape[0], 1))], axis=1)  # delta_l, column n-1 always in
+    X = np.abs(0.5 * (D @ A.T))  # (2^(n-1), n): |x_i| per subset
+    pre = np.cumprod(np.concatenate([np.ones((X.shape[0], 1)), X[:, :-1]], axis=1), axis=1)
+    suf = np.cumprod(np.concatenate([np.ones((X.shape[0], 1)), X[:, :0:-1]], axis=1), axis=1)[:, ::-1]
+    return (pre * suf).sum(axis=0)
+
+
+def _check_minors(G, A, oracle, cplx=False, rows=None, cols=None, scale=None):
+    n = A.shape[0]
+    S = _abs_scale(A) if scale is None and n <= 16 else scale
+    for k in rows if rows is not None else range(n):
+        for l in cols if cols is not None else range(n):
+            if n == 1:
+                want, bar = 1.0, 1.0
+            else:
+                M = _minor(A, k, l)
+                want = oracle.perm_c128(M) if cplx else oracle.perm_f64(M)
+                bar = oracle.perm_dp_f64(np.abs(M)) if n <= 21 else oracle.perm_f64(np.abs(M))
+            err = abs(G[k, l] - want)
+            assert err <= 1e-10 * bar, (k, l, err, bar)
+            if S is not None:
+                assert err <= TOL_S * S[k], (k, l, err, S[k])
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 7, 8, 9, 12, 16, 17, 20])
+def test_real_gradient_is_the_minor_permanents(pg, oracle, n):
+    A = syn.signed_real(n, 10000 + n)
+    p, G = pg.perm_grad(_dev(A))
+    G = G.cpu().numpy()
+    _check_minors(G, A, oracle)
+    scale = oracle.perm_dp_f64(np.abs(A)) if n <= 20 else 1.0
+    assert abs(p - oracle.perm_f64(A)) <= 1e-12 * scale
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 6, 8, 9, 13, 16, 17, 22])
+def test_complex_gradient_is_the_minor_permanents(pg, oracle, n):
+    A = syn.haar_unitary(max(n, 1), 10100 + n)
+    p, G = pg.perm_grad(_dev(A))
+    G = G.cpu().numpy()
+    _check_minors(G, A, oracle, cplx=True, rows=None if n <= 16 else (0, n // 2, n - 1))
+    assert abs(p - oracle.perm_c128(A)) <= 1e-12
+
+
+def test_positive_real_matches_the_subset_dp(pg, oracle):
+    # positive entries: the DP is free of cancellation, so this measures the
+    # gradient's true relative error on an ill-conditioned Ryser sum
+    n = 18
+    A = syn.uniform_real(n, 10200)
+    _, G = pg.perm_grad(_dev(A))
+    G = G.cpu().numpy()
+    for k, l in ((0, 0), (5, 11), (17, 3), (17, 17)):
+        want = oracle.perm_dp_f64(_minor(A, k, l))
+        assert abs(G[k, l] - want) <= 1e-10 * want
+
+
+def test_closed_forms(pg):
+    import torch
+
+    # J_n: every minor is J_(n-1), G = (n-1)! everywhere (the all-equal
+    # matrix is Ryser's worst cancellation: S_k / G_kl is about 40 at n = 16)
+    for n in (5, 11, 16):
+        J = np.ones((n, n))
+        _, G = pg.perm_grad(_dev(J))
+        want = math.factorial(n - 1)
+        S = _abs_scale(J)
+        assert np.max(np.abs(G.cpu().numpy() - want)) <= min(TOL_S * S[0], 1e-10 * want)
+    # diagonal: G_kk = prod_{i != k} a_ii; off-diagonal minors have a zero row.
+    # Here S_k = prod_{i != k} a_ii exactly.
+    d = 0.5 + syn.rng(10301).random(12)
+    p, G = pg.perm_grad(_dev(np.diag(d)))
+    G = G.cpu().numpy()
+    for k in range(12):
+        Sk = np.prod(np.delete(d, k))
+        assert abs(G[k, k] - Sk) <= TOL_S * Sk
+        assert np.max(np.abs(np.delete(G[k], k))) <= TOL_S * Sk
+    assert p == pytest.approx(np.prod(d), rel=1e-13)
+    # 2 x 2: perm = ad + bc, G = [[d, c], [b, a]]
+    p, G = pg.perm_grad(_dev(np.array([[1.5, -2.0], [0.25, 3.0]])))
+    assert G.cpu().numpy().tolist() == [[3.0, 0.25], [-2.0, 1.5]]
+    assert p == 1.5 * 3.0 + (-2.0) * 0.25
+    # n = 0: the empty permanent, no entries
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    st = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    pg.perm_grad_async(torch.zeros((0, 0), dtype=torch.float64, device="cuda"), out,
+                       torch.zeros((0, 0), dtype=torch.float64, device="cuda"), st)
+    torch.cuda.synchronize()
+    assert out.item() == 1.0 and st.item() == 0
+
+
+def test_zero_rows_and_bad_input(pg, oracle):
+    A = syn.signed_real(9, 10400)
+    A[4] = 0.0
+    p, G = pg.perm_grad(_dev(A))
+    G = G.cpu().numpy()
+    assert p == 0.0
+    assert np.all(G[np.arange(9) != 4] == 0.0)
+    for l in range(9):
+        assert abs(G[4, l] - oracle.perm_f64(_minor(A, 4, l))) <= 1e-13 * oracle.perm_dp_f64(np.abs(_minor(A, 4, l)))
+    A[7] = 0.0
+    p, G = pg.perm_grad(_dev(A))
+    assert p == 0.0 and not np.any(G.cpu().numpy())
+    B = syn.signed_real(6, 10401)
+    B[2, 3] = np.nan
+    with pytest.raises(pg.PermError):
+        pg.perm_grad(_dev(B))
+
+
+def test_row_expansion_identity(pg):
+    for n, seed in ((9, 1), (16, 2), (23, 3), (32, 4)):
+        A = syn.signed_real(n, 11000 + seed)
+        p, G = pg.perm_grad(_dev(A))
+        G = G.cpu().numpy()
+        scale = pg.perm(_dev(np.abs(A)))
+        for i in range(n):
+            dot = float(np.dot(A[i], G[i]))
+            assert abs(dot - p) <= 1e-10 * scale
+            assert abs(dot - p) <= 1e-9 * float(np.sum(np.abs(A[i] * G[i])))
+        assert abs(float(np.sum(A * G)) - n * p) <= 1e-9 * float(np.sum(np.abs(A * G)))
+        assert abs(p - pg.perm(_dev(A))) <= 1e-9 * float(np.sum(np.abs(A[0] * G[0])))
+
+
+def test_central_differences_of_the_oracle(pg, oracle):
+    # perm is affine in each entry, so the central difference is exact up to
+    # the oracle's rounding, for any step h
+    n = 10
+    A = syn.uniform_real(n, 12000)
+    _, G = pg.perm_grad(_dev(A))
+    G = G.cpu().numpy()
+    for k, l in ((0, 0), (3, 7), (9, 2), (5, 9)):
+        h = 0.25
+        Ap, Am = A.copy(), A.copy()
+        Ap[k, l] += h
+        Am[k, l] -= h
+        fd = (oracle.perm_dp_f64(Ap) - oracle.perm_dp_f64(Am)) / (2 * h)
+        assert fd == pytest.approx(G[k, l], rel=1e-12)
+
+
+def test_deterministic(pg):
+    A = _dev(syn.signed_real(21, 12050))
+    _, G1 = pg.perm_grad(A)
+    _, G2 = pg.perm_grad(A)
+    assert bool((G1 == G2).all())
+
+
+def test_batched_equals_single(pg, oracle):
+    import torch
+
+    Ms = np.stack(syn.boson_submatrices(40, 12060, 11, 11, 64))
+    out, G = pg.perm_grad_batched(_dev(Ms))
+    out, G = out.cpu().numpy(), G.cpu().numpy()
+    for p in (0, 17, 39):
+        v, Gs = pg.perm_grad(_dev(Ms[p]))
+        assert abs(out[p] - v) <= 1e-13
+        assert np.max(np.abs(G[p] - Gs.cpu().numpy())) <= 1e-13
+        assert abs(out[p] - oracle.perm_c128(Ms[p])) <= 1e-12
+    _check_minors(G[5], Ms[5], oracle, cplx=True)
+    R = np.stack([syn.signed_real(7, 12070 + i) for i in range(300)])
+    out, G = pg.perm_grad_batched(_dev(R))
+    out, G = out.cpu().numpy(), G.cpu().numpy()
+    for p in (0, 150, 299):
+        assert abs(out[p] - oracle.perm_f64(R[p])) <= 1e-13 * oracle.perm_dp_f64(np.abs(R[p]))
+        _check_minors(G[p], R[p], oracle)
+    R[77, 1, 1] = np.inf
+    with pytest.raises(pg.PermError):
+        pg.perm_grad_batched(_dev(R))
+
+
+def test_autograd_function(pg):
+    import torch
+
+    A = torch.from_numpy(syn.signed_real(7, 12100)).cuda().requires_grad_(True)
+    y = pg.permanent(A)
+    y.backward()
+    _, G = pg.perm_grad(A.detach())
+    assert torch.equal(A.grad, G)
+    B = torch.from_numpy(syn.signed_real(5, 12200)).cuda().requires_grad_(True)
+    assert torch.autograd.gradcheck(pg.permanent, (B,), eps=1e-3, atol=1e-9, rtol=1e-9)
+    C = torch.from_numpy(syn.haar_unitary(4, 12300)).cuda().requires_grad_(True)
+    assert torch.autograd.gradcheck(pg.permanent, (C,), eps=1e-4, atol=1e-9, rtol=1e-7)
+    Bt = torch.from_numpy(np.stack(syn.boson_submatrices(6, 12400, 5, 5, 16))).cuda().requires_grad_(True)
+    assert torch.autograd.gradcheck(lambda X: pg.permanent(X).abs().pow(2).sum(), (Bt,), eps=1e-4, atol=1e-9,
+                                    rtol=1e-7)
+
+
+def test_config_real_n28(pg, oracle):
+    """Dense real n=28 uniform [-1, 1): sampled minors from the oracle and the
+    identity sum_j a_ij G_ij = perm for every row."""
+    A = syn.grad_real_28()
+    n = 28
+    p, G = pg.perm_grad(_dev(A))
+    G = G.cpu().numpy()
+    for i in range(n):
+        assert abs(float(np.dot(A[i], G[i])) - p) <= 1e-9 * float(np.sum(np.abs(A[i] * G[i])))
+    for k, l in ((0, 27), (13, 4), (27, 27)):
+        want = oracle.perm_f64(_minor(A, k, l))
+        assert abs(G[k, l] - want) <= 1e-10 * pg.perm(_dev(np.abs(_minor(A, k, l))))
+        assert abs(G[k, l] - want) <= 1e-9 * abs(want)
+
+
+def test_config_complex_batch_1024_k16(pg, oracle):
+    """1024 complex 16 x 16 Haar submatrices in one batched launch: sampled
+    matrices' full gradients against the oracle's minors."""
+    Ms = syn.grad_boson_16(1024)
+    out, G = pg.perm_grad_batched(_dev(Ms))
+    out, G = out.cpu().numpy(), G.cpu().numpy()
+    for p in (0, 511, 1023):
+        assert abs(out[p] - oracle.perm_c128(Ms[p])) <= 1e-12
+        _check_minors(G[p], Ms[p], oracle, cplx=True)
