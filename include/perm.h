@@ -132,8 +132,8 @@ int perm_sparse(int n, const int32_t* cptrs, const int32_t* rids, const double* 
                 double* out, int32_t* status, void* stream);
 
 /*
- * Batched complex permanents (boson-sampling style: thousands of small k x k
- * matrices of uneven sizes).  Each matrix is the sweep of perm() (Alg. 1 over
+ * Batched permanents (boson-sampling style: thousands of small k x k
+ * matrices of uneven sizes; complex, or real).  Each matrix is the sweep of perm() (Alg. 1 over
  * complex entries, Alg. 3 chunks of Sec. 3.1.1); all of them run in one
  * CUDA-graph replay: a prep kernel (fixed-point tables), one persistent
  * kernel that pops work items (32 matrices of one size per warp for short
@@ -143,11 +143,13 @@ int perm_sparse(int n, const int32_t* cptrs, const int32_t* rids, const double* 
  *
  * perm_batched_plan_create - build a plan (host call; allocates the plan's
  *   device buffers and captures the graph; synchronous).
- *     type       PERM_C128 (the only batched type).
+ *     type       PERM_C128 or PERM_F64 (one type per plan).
  *     ns_host    host int[count], sizes k in 1..32.
- *     A_packed   device double pairs: matrix m, row-major, starts at complex
- *                element offsets_host[m] (host int64[count]).
- *     out        device double[2*count]: (re, im) of perm of every matrix.
+ *     A_packed   device; PERM_C128: double pairs, PERM_F64: doubles; matrix
+ *                m is row-major and starts at element offsets_host[m]
+ *                (host int64[count]).
+ *     out        device; PERM_C128: double[2*count], (re, im) of perm of
+ *                every matrix; PERM_F64: double[count].
  *     status     device int32[count] or NULL (perm() status per matrix).
  *   A_packed, out and status are bound to the plan: every perm_batched()
  *   replay reads and writes these buffers.

@@ -313,32 +313,38 @@ def permanent(A):
 
 
 class BatchPlan:
-    """A batched plan over a list of square complex128 matrices (perm_batched_*).
+    """A batched plan over a list of square matrices (perm_batched_*), all
+    complex128 or all float64 (dtype picks; default: complex128 unless every
+    input is real and dtype="float64").
 
     The matrices are packed into one device buffer owned by the plan; run()
     replays the captured graph (one launch) and returns the device results."""
 
-    def __init__(self, mats, device=None, autotune_rounds: int = 0, stream=None):
+    def __init__(self, mats, device=None, autotune_rounds: int = 0, stream=None, dtype="complex128"):
         torch = _torch()
         lib = load()
         device = device or torch.device("cuda")
+        real = str(dtype) in ("float64", "torch.float64", "<class 'numpy.float64'>")
+        self.type = PERM_F64 if real else PERM_C128
         ks = [int(m.shape[0]) for m in mats]
         offs, total = [], 0
         for k in ks:
             offs.append(total)
             total += k * k
-        host = np.zeros(total, dtype=np.complex128)
+        host = np.zeros(total, dtype=np.float64 if real else np.complex128)
         for m, o in zip(mats, offs):
             a = m.detach().cpu().numpy() if hasattr(m, "detach") else np.asarray(m)
-            host[o:o + a.size] = np.asarray(a, dtype=np.complex128).reshape(-1)
+            if real and np.iscomplexobj(a):
+                raise TypeError("dtype float64 needs real matrices")
+            host[o:o + a.size] = np.asarray(a, dtype=host.dtype).reshape(-1)
         self.A = torch.from_numpy(host).to(device)
-        self.out = torch.zeros(2 * len(ks), dtype=torch.float64, device=device)
+        self.out = torch.zeros((1 if real else 2) * len(ks), dtype=torch.float64, device=device)
         self.status = torch.full((len(ks),), -1, dtype=torch.int32, device=device)
         self.ks = ks
         self._plan = ctypes.c_void_p(0)
         karr = (ctypes.c_int * len(ks))(*ks)
         oarr = (ctypes.c_int64 * len(ks))(*offs)
-        check(lib.perm_batched_plan_create(ctypes.byref(self._plan), PERM_C128, karr, len(ks),
+        check(lib.perm_batched_plan_create(ctypes.byref(self._plan), self.type, karr, len(ks),
                                            ctypes.c_void_p(self.A.data_ptr()), oarr,
                                            ctypes.c_void_p(self.out.data_ptr()),
                                            ctypes.c_void_p(self.status.data_ptr())), "perm_batched_plan_create")
@@ -351,7 +357,7 @@ class BatchPlan:
         check(load().perm_batched(self._plan, h), "perm_batched")
 
     def run(self, stream=None):
-        """Replay and return a numpy complex128 array of the permanents."""
+        """Replay and return a numpy array of the permanents (complex128 or float64)."""
         self.run_async(stream)
         _, s = _stream_handle(stream)
         s.synchronize()
@@ -360,7 +366,7 @@ class BatchPlan:
         if len(bad):
             check(int(st[bad[0]]), f"perm_batched (matrix {int(bad[0])})")
         o = self.out.cpu().numpy()
-        return o[0::2] + 1j * o[1::2]
+        return o.copy() if self.type == PERM_F64 else o[0::2] + 1j * o[1::2]
 
     def info(self, k: int):
         mode, c, n = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()

@@ -1,5 +1,5 @@
-// Batched complex permanents: thousands of k x k matrices of uneven sizes in
-// one CUDA-graph replay (prep kernel, one persistent work-queue kernel,
+// Batched permanents (complex or real): thousands of k x k matrices of uneven
+// sizes in one CUDA-graph replay (prep kernel, one persistent work-queue kernel,
 // finish kernel).  Each matrix is the Ryser / Nijenhuis-Wilf sweep of the
 // single-matrix complex kernel (Alg. 1 over complex entries, chunked as
 // Alg. 3 with power-of-two chunks, Sec. 3.1.1):
@@ -12,6 +12,9 @@
 //  * The chunk exponent and the lane/warp mode of every size class come from
 //    a heuristic or from perm_batched_autotune, which times the candidates
 //    on the plan's own matrices.
+//  * Real matrices run the integer product chains of the single-matrix real
+//    kernel (odd fixed-point rows, 62-bit mantissas), complex ones those of
+//    the complex kernel.
 //  * The prep kernel rounds every matrix once to fixed point (as the
 //    single-matrix kernel) into a plan-owned table that the main kernel reads
 //    through L1 (column reads are warp broadcasts in the chunked mode).
@@ -29,6 +32,7 @@
 #include "common.cuh"
 #include "complex.cuh"
 #include "kernels.h"
+#include "real.cuh"
 
 namespace permgpu {
 
@@ -66,6 +70,7 @@ struct BatchArgs {
   int32_t* status;        // per matrix (optional)
   int nmats;
   int nitems;
+  int type;               // PERM_C128 or PERM_F64
 };
 
 // One CTA per matrix: D[(2j+s) k + i], base[k], zero[k] as in cplx_stage.
@@ -85,7 +90,39 @@ __global__ void __launch_bounds__(kBlock) batch_prep_kernel(BatchArgs a) {
   }
   __syncthreads();
   const int i = threadIdx.x;
-  if (i < k) {
+  if (a.type == PERM_F64) {
+    // real: odd fixed-point rows as in real_stage (Y = 2 x 2^s)
+    long long* RD = reinterpret_cast<long long*>(a.table + bm.d_off);
+    long long* rbase = RD + (size_t)2 * (k > 1 ? k - 1 : 0) * k;
+    long long* rzero = rbase + k;
+    if (i < k) {
+      const double* row = a.A + bm.a_off + (int64_t)i * k;
+      double absum = 0.0;
+      int fin = 1;
+      for (int j = 0; j < k; ++j) {
+        const double v = row[j];
+        fin &= isfinite(v) ? 1 : 0;
+        absum += fabs(v);
+      }
+      int kk = 0;
+      if (fin && absum > 0.0) frexp(absum, &kk);
+      const int s = 61 - kk;
+      long long qsum = 0;
+      for (int j = 0; j < k - 1; ++j) {
+        const long long q = fin ? __double2ll_rn(ldexp(row[j], s - 1)) : 0;
+        qsum += 2 * q;
+        RD[(2 * j) * k + i] = 4 * q;
+        RD[(2 * j + 1) * k + i] = -4 * q;
+      }
+      const long long qn = fin ? 2 * __double2ll_rd(ldexp(row[k - 1], s - 1)) + 1 : 1;
+      rbase[i] = qn - qsum;
+      rzero[i] = 0;
+      atomicAdd(&s_sum, s);
+      atomicAdd(&s_bound, kk - 1);
+      if (!fin) atomicOr(&s_flags, 1);
+      if (fin && absum == 0.0) atomicOr(&s_flags, 2);
+    }
+  } else if (i < k) {
     const double* row = a.A + 2 * (bm.a_off + (int64_t)i * k);
     double absum = 0.0;
     int fin = 1;
@@ -189,6 +226,90 @@ __device__ __forceinline__ void batch_sweep(const longlong2* __restrict__ D, int
   acci = dd_make(acci.hi, acci.lo);
 }
 
+// The real counterpart of batch_sweep: two integer product chains as in
+// ryser_real_kernel, the term split exactly into head and tail.
+template <int K>
+__device__ __forceinline__ void batch_sweep_real(const long long* __restrict__ D, int sum_s, int c, uint64_t g0,
+                                                 bool active, dd& acc) {
+  const long long* base = D + (size_t)2 * (K > 1 ? K - 1 : 0) * K;
+  const long long* zero = base + K;
+  const int K1 = 64 * K + 1025 - sum_s;
+  const uint32_t nsteps = 1u << c;
+  const uint32_t kb = (uint32_t)((g0 >> c) & 1u) << c;
+  const uint32_t gpar = (uint32_t)(g0 & 1u);
+  unsigned long long Y[K];
+#pragma unroll
+  for (int i = 0; i < K; ++i) Y[i] = (unsigned long long)__ldg(base + i);
+  const uint64_t G = gray64(g0);
+  for (int j = (c > 0 ? c - 1 : 0); j < K - 1; ++j) {
+    const long long msk = -(long long)((G >> j) & 1u);
+    const long long* col = D + (size_t)(2 * j) * K;
+#pragma unroll
+    for (int i = 0; i < K; ++i) Y[i] += (unsigned long long)(__ldg(col + i) & msk);
+  }
+  for (uint32_t t = 0; t < nsteps; ++t) {
+    const int j = __ffs(t) - 1;
+    const uint32_t sb = ((t | kb) >> (j + 1)) & 1u;
+    const long long* col = t ? D + (size_t)(2 * j + sb) * K : zero;
+    Prod pa, pb;
+    prod_init(pa);
+    prod_init(pb);
+    uint32_t neg = 0, epos = 0;
+#pragma unroll
+    for (int i = 0; i < K; i += 2) {
+      uint32_t a0, a1, ma, b0, b1, mb = 0, qb = 0;
+      Y[i] += (unsigned long long)__ldg(col + i);
+      row_abs(Y[i], a0, a1, ma);
+      if (i + 1 < K) {
+        Y[i + 1] += (unsigned long long)__ldg(col + i + 1);
+        row_abs(Y[i + 1], b0, b1, mb);
+      }
+      const uint32_t qa = prod_mul(pa, a0, a1);
+      if (i + 1 < K) qb = prod_mul(pb, b0, b1);
+      neg = neg + ma + mb;
+      epos = epos + qa + qb;
+    }
+    epos += prod_mul(pa, pb.m0, pb.m1);
+    const int shifts = 30 * (K + 1) - (int)epos;
+    const int f = K1 - shifts - (K + 1);
+    const uint32_t signbit = (neg ^ t ^ gpar) << 31;
+    double th, tl;
+    prod_to_dd(pa, (uint32_t)max(f, 0), signbit, th, tl);
+    dd_acc(acc, active ? th : 0.0, active ? tl : 0.0);
+  }
+  acc = dd_make(acc.hi, acc.lo);
+}
+
+template <int K>
+__device__ __forceinline__ void batch_item_real(const BatchArgs& a, const BatchItem& it) {
+  const int lane = threadIdx.x & 31;
+  dd acc = {0.0, 0.0};
+  const dd zero = {0.0, 0.0};
+  if (it.mode == kLaneMode) {
+    const bool active = lane < it.count;
+    const int m = a.lane_mats[it.mat + (active ? lane : 0)];
+    const BatchMat bm = a.mats[m];
+    const bool ok = active && bm.flags == 0;
+    batch_sweep_real<K>(reinterpret_cast<const long long*>(a.table + bm.d_off), bm.sum_s, K - 1, 0ull, ok, acc);
+    if (active) {
+      a.slots[2 * bm.slot0] = acc;
+      a.slots[2 * bm.slot0 + 1] = zero;
+    }
+  } else {
+    const BatchMat bm = a.mats[it.mat];
+    const uint64_t chunk = (uint64_t)it.chunk0 + lane;
+    const uint64_t nchunks = 1ull << (K - 1 - it.c);
+    const bool active = chunk < nchunks && bm.flags == 0;
+    batch_sweep_real<K>(reinterpret_cast<const long long*>(a.table + bm.d_off), bm.sum_s, it.c,
+                        (active ? chunk : 0ull) << it.c, active, acc);
+    acc = dd_warp_sum(acc);
+    if (lane == 0) {
+      a.slots[2 * it.slot] = acc;
+      a.slots[2 * it.slot + 1] = zero;
+    }
+  }
+}
+
 template <int K>
 __device__ __forceinline__ void batch_item(const BatchArgs& a, const BatchItem& it) {
   const int lane = threadIdx.x & 31;
@@ -227,9 +348,12 @@ __global__ void __launch_bounds__(kBlock, 1) batch_main_kernel(BatchArgs a) {
     if (idx >= a.nitems) break;
     const BatchItem it = a.items[idx];
     switch (it.k) {
-#define PERM_BATCH_CASE(KK) \
-  case KK:                  \
-    batch_item<KK>(a, it);  \
+#define PERM_BATCH_CASE(KK)       \
+  case KK:                        \
+    if (a.type == PERM_F64)       \
+      batch_item_real<KK>(a, it); \
+    else                          \
+      batch_item<KK>(a, it);      \
     break;
       PERM_BATCH_CASE(1) PERM_BATCH_CASE(2) PERM_BATCH_CASE(3) PERM_BATCH_CASE(4) PERM_BATCH_CASE(5)
       PERM_BATCH_CASE(6) PERM_BATCH_CASE(7) PERM_BATCH_CASE(8) PERM_BATCH_CASE(9) PERM_BATCH_CASE(10)
@@ -260,7 +384,9 @@ __global__ void batch_finish_kernel(BatchArgs a, const int32_t* nslots) {
   int32_t st = PERM_OK;
   if (bm.flags & 1) st = PERM_EINVAL;
   else if (bm.flags & 4) st = PERM_ERANGE;
-  if (st != PERM_OK) {
+  if (a.type == PERM_F64) {
+    a.out[m] = st != PERM_OK ? nan : (bm.flags & 2) ? 0.0 : (r.hi + r.lo) * f;
+  } else if (st != PERM_OK) {
     a.out[2 * m] = nan;
     a.out[2 * m + 1] = nan;
   } else if (bm.flags & 2) {
@@ -279,6 +405,7 @@ using namespace permgpu;
 
 struct perm_batch_plan {
   int device = 0;
+  int type = PERM_C128;
   int count = 0;
   int sms = 0;
   int max_k = 0;
@@ -352,7 +479,9 @@ static int batch_build(perm_batch_plan* p) {
     mats[m].flags = 0;
     mats[m].a_off = p->a_off[m];
     mats[m].d_off = (int64_t)toff;
-    toff += (size_t)2 * (k > 1 ? k - 1 : 0) * k + 2 * (size_t)k;
+    const size_t elems = (size_t)2 * (k > 1 ? k - 1 : 0) * k + 2 * (size_t)k;
+    // complex: one longlong2 per entry; real: two int64 per longlong2
+    toff += p->type == PERM_F64 ? (elems + 1) / 2 : elems;
   }
   p->table_elems = toff;
   // slots: lane-mode matrices one slot, warp-mode one per item
@@ -467,6 +596,7 @@ static BatchArgs batch_args(const perm_batch_plan* p) {
   a.status = p->status;
   a.nmats = p->count;
   a.nitems = p->nitems;
+  a.type = p->type;
   return a;
 }
 
@@ -509,9 +639,10 @@ extern "C" int perm_batched_plan_create(perm_batch_plan** plan, int type, const 
                                         int32_t* status) {
   if (!plan) return PERM_EINVAL;
   *plan = nullptr;
-  if (type != PERM_C128) return PERM_EINVAL;
+  if (type != PERM_C128 && type != PERM_F64) return PERM_EINVAL;
   if (count < 1 || !ns_host || !offsets_host || !A_packed || !out) return PERM_EINVAL;
   perm_batch_plan* p = new perm_batch_plan();
+  p->type = type;
   if (cudaGetDevice(&p->device) != cudaSuccess ||
       cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) {
     delete p;
@@ -579,6 +710,7 @@ extern "C" int perm_batched_autotune(perm_batch_plan* plan, int rounds, void* st
     Cand pick = {plan->cls_mode[k], plan->cls_c[k]};
     for (const Cand& cd : cands) {
       perm_batch_plan* q = new perm_batch_plan();
+      q->type = plan->type;
       q->device = plan->device;
       q->sms = plan->sms;
       q->count = (int)ks.size();

@@ -390,9 +390,9 @@ int perm_decomp_eval(perm_decomp* p, double* out, void* stream) {
     return PERM_OK;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  // Leaves of order 2..32 go to one batched launch (the complex batched plan,
-  // entries embedded with zero imaginary parts); larger ones get their own
-  // launch of the dense kernel (density >= 30 %) or the sparse kernel.
+  // Leaves of order 2..32 go to one batched launch (real batched plan);
+  // larger ones get their own launch of the dense kernel (density >= 30 %)
+  // or the sparse kernel.
   const size_t L = d.leaves.size();
   std::vector<size_t> off_dense(L, 0), off_cp(L, 0), off_nz(L, 0);
   std::vector<int64_t> leaf_nnz(L, 0), boff;
@@ -412,10 +412,7 @@ int perm_decomp_eval(perm_decomp* p, double* out, void* stream) {
       bidx[l] = (int)bks.size();
       bks.push_back(m.n);
       boff.push_back((int64_t)nb);
-      for (double v : m.a) {
-        hb.push_back(v);
-        hb.push_back(0.0);
-      }
+      hb.insert(hb.end(), m.a.begin(), m.a.end());
       nb += m.a.size();
     } else if (cnt * 10 >= (size_t)m.n * m.n * 3) {
       kind[l] = 2;
@@ -443,7 +440,7 @@ int perm_decomp_eval(perm_decomp* p, double* out, void* stream) {
   }
   const size_t nbat = bks.size();
   const size_t bytes =
-      sizeof(double) * (nd + nnz + L + 2 * nb + 2 * nbat) + sizeof(int32_t) * (ncp + nnz + L + nbat) + 64;
+      sizeof(double) * (nd + nnz + L + nb + nbat) + sizeof(int32_t) * (ncp + nnz + L + nbat) + 64;
   void* ws = nullptr;
   if (cudaMalloc(&ws, bytes) != cudaSuccess) {
     cudaGetLastError();
@@ -453,8 +450,8 @@ int perm_decomp_eval(perm_decomp* p, double* out, void* stream) {
   double* dd_vals = dd_dense + nd;
   double* dd_out = dd_vals + nnz;
   double* dd_bat = dd_out + L;
-  double* dd_bout = dd_bat + 2 * nb;
-  int32_t* di_cp = reinterpret_cast<int32_t*>(dd_bout + 2 * nbat);
+  double* dd_bout = dd_bat + nb;
+  int32_t* di_cp = reinterpret_cast<int32_t*>(dd_bout + nbat);
   int32_t* di_r = di_cp + ncp;
   int32_t* di_st = di_r + nnz;
   int32_t* di_bst = di_st + L;
@@ -466,10 +463,10 @@ int perm_decomp_eval(perm_decomp* p, double* out, void* stream) {
   cp(dd_vals, hv.data(), sizeof(double) * nnz);
   cp(di_cp, hcp.data(), sizeof(int32_t) * ncp);
   cp(di_r, hr.data(), sizeof(int32_t) * nnz);
-  cp(dd_bat, hb.data(), sizeof(double) * 2 * nb);
+  cp(dd_bat, hb.data(), sizeof(double) * nb);
   perm_batch_plan* plan = nullptr;
   if (rc == PERM_OK && nbat) {
-    rc = perm_batched_plan_create(&plan, PERM_C128, bks.data(), (int)nbat, dd_bat, boff.data(), dd_bout, di_bst);
+    rc = perm_batched_plan_create(&plan, PERM_F64, bks.data(), (int)nbat, dd_bat, boff.data(), dd_bout, di_bst);
     if (rc == PERM_OK) rc = perm_batched(plan, stream);
   }
   for (size_t l = 0; l < L && rc == PERM_OK; ++l) {
@@ -480,14 +477,14 @@ int perm_decomp_eval(perm_decomp* p, double* out, void* stream) {
       rc = perm_sparse(m.n, di_cp + off_cp[l], di_r + off_nz[l], dd_vals + off_nz[l], leaf_nnz[l], dd_out + l,
                        di_st + l, stream);
   }
-  std::vector<double> vals(L, 1.0), bvals(2 * nbat, 0.0);
+  std::vector<double> vals(L, 1.0), bvals(nbat, 0.0);
   std::vector<int32_t> sts(L, 0), bsts(nbat, 0);
   auto back = [&](void* dst, const void* src, size_t n) {
     if (rc == PERM_OK && n && cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToHost, s) != cudaSuccess) rc = PERM_ECUDA;
   };
   back(vals.data(), dd_out, sizeof(double) * L);
   back(sts.data(), di_st, sizeof(int32_t) * L);
-  back(bvals.data(), dd_bout, sizeof(double) * 2 * nbat);
+  back(bvals.data(), dd_bout, sizeof(double) * nbat);
   back(bsts.data(), di_bst, sizeof(int32_t) * nbat);
   if (cudaStreamSynchronize(s) != cudaSuccess && rc == PERM_OK) rc = PERM_ECUDA;
   if (plan) perm_batched_plan_destroy(plan);
@@ -499,7 +496,7 @@ int perm_decomp_eval(perm_decomp* p, double* out, void* stream) {
   for (size_t l = 0; l < L; ++l) {
     if (kind[l] == 1) {
       sts[l] = bsts[bidx[l]];
-      vals[l] = bvals[2 * bidx[l]];
+      vals[l] = bvals[bidx[l]];
     }
   }
   std::vector<hdd> block(d.nblocks, hdd{0.0, 0.0});

@@ -194,8 +194,13 @@ __device__ __forceinline__ void yadd(longlong2& y, longlong2 d) {
 }
 __device__ __forceinline__ double aadd(double a, double b) { return a + b; }
 __device__ __forceinline__ double2 aadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ double aneg(double a, bool neg) { return neg ? -a : a; }
-__device__ __forceinline__ double2 aneg(double2 a, bool neg) { return neg ? make_double2(-a.x, -a.y) : a; }
+// Sign flips as an integer xor of the high word: one ALU op, so that the
+// column-flip update costs a single DADD on the (1/64-rate) FP64 pipe.
+__device__ __forceinline__ double aneg(double a, bool neg) {
+  const uint32_t m = neg ? 0x80000000u : 0u;
+  return __hiloint2double((int)((uint32_t)__double2hiint(a) ^ m), __double2loint(a));
+}
+__device__ __forceinline__ double2 aneg(double2 a, bool neg) { return make_double2(aneg(a.x, neg), aneg(a.y, neg)); }
 __device__ __forceinline__ double asel(double a, bool keep) { return keep ? a : 0.0; }
 __device__ __forceinline__ double2 asel(double2 a, bool keep) { return keep ? a : make_double2(0.0, 0.0); }
 

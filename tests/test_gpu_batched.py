@@ -66,3 +66,38 @@ def test_invalid_entries_flagged(pg):
     st = plan.status.cpu().numpy()
     assert st[2] == 1 and (np.delete(st, 2) == 0).all()
     plan.close()
+
+
+def test_real_plan_uneven_sizes_vs_oracle(pg, oracle):
+    """float64 plans: the integer product chains of the real kernel per matrix,
+    lane mode (small k) and chunked mode (k > 14)."""
+    g = syn.rng(15)
+    ks = [1, 2, 3, 5, 8, 11, 14, 15, 18, 21] * 12
+    mats = [2.0 * g.random((k, k)) - 1.0 for k in ks]
+    plan = pg.BatchPlan(mats, dtype="float64")
+    got = plan.run()
+    assert got.dtype == np.float64
+    for m, v in zip(mats, got):
+        want = oracle.perm_dp_f64(m)
+        assert abs(v - want) <= 1e-13 * oracle.perm_dp_f64(np.abs(m))
+    assert np.array_equal(plan.run(), got)
+    plan.close()
+
+
+def test_real_plan_matches_single_matrix_kernel_and_autotune(pg):
+    import torch
+
+    mats = [syn.uniform_real(k, 1600 + k) for k in range(16, 25)] * 3
+    plan = pg.BatchPlan(mats, dtype="float64", autotune_rounds=1)
+    got = plan.run()
+    for m, v in zip(mats, got):
+        single = pg.perm(torch.from_numpy(np.ascontiguousarray(m)).cuda())
+        assert v == pytest.approx(single, rel=1e-13)
+    plan.close()
+    bad = [syn.signed_real(4, 1700), syn.signed_real(5, 1701)]
+    bad[1][2, 2] = np.inf
+    plan = pg.BatchPlan(bad, dtype="float64")
+    with pytest.raises(pg.PermError):
+        plan.run()
+    assert plan.status.cpu().numpy().tolist() == [0, 1]
+    plan.close()

@@ -44,15 +44,26 @@ def test_shuffled_block_diagonal_n44(dec, oracle):
     assert got == pytest.approx(want, rel=1e-10)
 
 
+def _min_degree_core(n, seed, perms):
+    """Union of random permutation matrices: every line keeps more than four
+    nonzeros (so Alg. 4 leaves it whole) at density about perms / n."""
+    g = syn.rng(seed)
+    while True:
+        M = np.zeros((n, n))
+        for _ in range(perms):
+            M[np.arange(n), g.permutation(n)] = 1.0
+        if min((M != 0).sum(0).min(), (M != 0).sum(1).min()) > 4:
+            return M * (0.25 + g.random((n, n)))
+
+
 def test_large_leaves_use_the_single_matrix_kernels(dec):
-    """Leaves of order > 32: a 34 x 34 core (dense, then sparse) with two
-    extra rows / columns of two nonzeros that the expansion folds away;
-    checked against the dense GPU kernel on the full matrix."""
+    """Leaves of order > 32: a 34 x 34 core (dense, then sparse at density
+    about 0.2) with two extra rows / columns of two nonzeros that the expansion
+    folds away; checked against the dense GPU kernel on the full matrix."""
     import paper_2502_16577_gb300 as pg
     import torch
 
-    for density in (0.5, 0.2):
-        core = syn.sparse_real(34, 1400 + int(10 * density), density)
+    for core in (syn.uniform_real(34, 1410) + 0.1, _min_degree_core(34, 1420, 7)):
         n = 36
         A = np.zeros((n, n))
         A[:34, :34] = core
@@ -61,7 +72,7 @@ def test_large_leaves_use_the_single_matrix_kernels(dec):
         A[5, 35] = 0.25
         A[20, 34] = 0.5
         got, info = dec.perm_sparse_decomp(A)
-        assert info["max_leaf_n"] > 32
+        assert info["max_leaf_n"] == 34
         want = pg.perm(torch.from_numpy(A).cuda())
         assert got == pytest.approx(want, rel=1e-10)
 
