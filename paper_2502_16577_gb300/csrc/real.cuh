@@ -78,23 +78,6 @@ __device__ __forceinline__ void row_abs(unsigned long long Y, uint32_t& a0, uint
   a1 = yhi ^ m;
 }
 
-// Y += d (two's complement), as a 64-bit multiply-add by one (a register the
-// compiler cannot fold) plus a 32-bit one on the high half, so that the row
-// update runs on the IMAD pipe next to the ALU-heavy normalisation.
-__device__ __forceinline__ void row_add(unsigned long long& Y, long long d, uint32_t one) {
-  uint32_t dlo = (uint32_t)(unsigned long long)d;
-  uint32_t dhi = (uint32_t)((unsigned long long)d >> 32);
-  asm("{\n\t"
-      ".reg .u32 lo, hi;\n\t"
-      "mad.wide.u32 %0, %1, %3, %0;\n\t"
-      "mov.b64 {lo, hi}, %0;\n\t"
-      "mad.lo.u32 hi, %2, %3, hi;\n\t"
-      "mov.b64 %0, {lo, hi};\n\t"
-      "}"
-      : "+l"(Y)
-      : "r"(dlo), "r"(dhi), "r"(one));
-}
-
 // The term sign * M * 2^(f+1-1023-62), M in [2^62, 2^63), as an unevaluated
 // sum hi + lo of two binary64 numbers with no rounding: hi is M rounded to 53
 // bits (the implicit bit placed on the exponent field f, the biased exponent
@@ -211,7 +194,6 @@ __global__ void __launch_bounds__(kBlock, (N <= 48 ? 2 : 1)) ryser_real_kernel(R
   // exponent bookkeeping, see prod_to_dd: the term is
   // sign * M * 2^(64N + 3 - sum_s - sum_lz - 62) in units of prod_i x_i.
   const int K1 = 64 * N + 1025 - sh.sum_s;
-  const uint32_t one = (uint32_t)a.one;  // 1, opaque to the compiler
   const bool bad = sh.nonfinite || sh.bound_log2 + N > 1000;
   const bool skip = bad || sh.zero_row;
 
@@ -260,10 +242,10 @@ __global__ void __launch_bounds__(kBlock, (N <= 48 ? 2 : 1)) ryser_real_kernel(R
       for (int p = 0; p < L::NP / 2; ++p) {
         const longlong2 d = col[p];
         uint32_t a0, a1, ma, b0, b1, mb = 0, qb = 0;
-        row_add(Y[2 * p], d.x, one);
+        Y[2 * p] += (unsigned long long)d.x;
         row_abs(Y[2 * p], a0, a1, ma);
         if (2 * p + 1 < N) {
-          row_add(Y[2 * p + 1], d.y, one);
+          Y[2 * p + 1] += (unsigned long long)d.y;
           row_abs(Y[2 * p + 1], b0, b1, mb);
         }
         const uint32_t qa = prod_mul(pa, a0, a1);
