@@ -93,7 +93,8 @@ static int launch_ryser(const KernelEntry& ke, const void* A, int n, uint64_t g_
   uint64_t k_begin = g_begin >> c;
   uint64_t k_end = (g_end + (1ull << c) - 1) >> c;
   uint64_t nchunks = g_end > g_begin ? k_end - k_begin : 0;
-  uint64_t groups = (nchunks + 31) / 32;
+  const uint64_t cpw = (uint64_t)(ke.chunks_per_warp > 0 ? ke.chunks_per_warp : 32);
+  uint64_t groups = (nchunks + cpw - 1) / cpw;
   uint64_t need = (groups + kWarps - 1) / kWarps;
   int grid = (int)(need < (uint64_t)grid_full ? (need > 0 ? need : 1) : grid_full);
 

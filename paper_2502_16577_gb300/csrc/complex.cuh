@@ -16,6 +16,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "real.cuh"
 
 namespace permgpu {
 
@@ -211,6 +212,189 @@ __global__ void __launch_bounds__(kBlock, (N <= 8 ? 2 : 1)) ryser_cplx_kernel(Ry
       const bool in = t - tlo < tcnt;
       dd_acc(accr, in ? hr * sc : 0.0, in ? lr * sc : 0.0);
       dd_acc(acci, in ? hi_ * sc : 0.0, in ? li * sc : 0.0);
+    }
+    accr = dd_make(accr.hi, accr.lo);
+    acci = dd_make(acci.hi, acci.lo);
+  }
+
+  dd blkr = dd_block_sum(accr);
+  dd blki = dd_block_sum(acci);
+  dd* part = static_cast<dd*>(a.part);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = blkr;
+    part[2 * blockIdx.x + 1] = blki;
+  }
+  if (!arrive_last(a.counter)) return;
+  if (threadIdx.x < 32) {
+    dd tr = {0.0, 0.0}, ti = {0.0, 0.0};
+    for (unsigned int b = threadIdx.x; b < gridDim.x; b += 32) {
+      tr = dd_add(tr, part[2 * b]);
+      ti = dd_add(ti, part[2 * b + 1]);
+    }
+    tr = dd_warp_sum(tr);
+    ti = dd_warp_sum(ti);
+    if (threadIdx.x == 0) {
+      double* out = static_cast<double*>(a.out);
+      int32_t st = PERM_OK;
+      if (sh.nonfinite) st = PERM_EINVAL;
+      else if (sh.bound_log2 + N > 1000) st = PERM_ERANGE;
+      const double nan = __longlong_as_double(0x7ff8000000000000ll);
+      if (a.mode == 0) {
+        const double f = (N & 1) ? 2.0 : -2.0;
+        out[0] = st != PERM_OK ? nan : (sh.zero_row ? 0.0 : (tr.hi + tr.lo) * f);
+        out[1] = st != PERM_OK ? nan : (sh.zero_row ? 0.0 : (ti.hi + ti.lo) * f);
+      } else {
+        out[0] = st != PERM_OK ? nan : tr.hi;
+        out[1] = st != PERM_OK ? 0.0 : tr.lo;
+        out[2] = st != PERM_OK ? nan : ti.hi;
+        out[3] = st != PERM_OK ? 0.0 : ti.lo;
+      }
+      if (a.status) *a.status = st;
+      *a.counter = 0u;
+    }
+  }
+}
+
+// ------------------------------------------------------------------------
+// Two lanes per chunk (n >= 16).  The single-lane kernel above holds all n
+// complex rows of its chunk in registers (about 255 registers at n = 32, one
+// CTA per SM).  Here lane pair (2m, 2m+1) walks one chunk: each lane keeps
+// half of the rows and one product chain, one shuffle and one complex
+// multiply combine the halves, so twice as many warps stay resident for
+// n + 2 instead of n + 1 complex multiplies per step.  Every term is computed
+// by both lanes of the pair; the lane whose parity matches the step keeps it,
+// and every second step both lanes split their kept term exactly into
+// binary64 head + tail (integer assembly) and add it to their double-double
+// partials.
+
+struct CTerm {
+  int32_t r1, i1;
+  uint32_t r0, i0;
+  int e;  // value = (r + i im) 2^e with r = r1 2^31 + r0
+};
+
+__device__ __forceinline__ CTerm cterm_mul(CTerm a, CTerm b) {
+  CProd p;
+  p.r1 = a.r1;
+  p.i1 = a.i1;
+  p.r0 = a.r0;
+  p.i0 = a.i0;
+  const long long br = ((long long)b.r1 << 31) | b.r0, bi = ((long long)b.i1 << 31) | b.i0;
+  const int s = cprod_mul(p, br, bi);
+  return CTerm{p.r1, p.i1, p.r0, p.i0, a.e + b.e + 62 - s};
+}
+
+// v 2^E (signed v, |v| < 2^62) as an exact head + tail (see prod_to_dd),
+// negated when neg is set; zero for v = 0 or below the normal range.
+__device__ __forceinline__ void cpart_to_dd(long long v, int E, uint32_t neg, double& h, double& l) {
+  const unsigned long long sgn = (unsigned long long)(v >> 63);
+  const unsigned long long mag = ((unsigned long long)v ^ sgn) - sgn;
+  const int lz = __clzll((long long)(mag | 1ull));
+  const unsigned long long nm = mag << (lz - 1);
+  Prod p;
+  p.m0 = (uint32_t)nm;
+  p.m1 = (uint32_t)(nm >> 32);
+  const int f = E - (lz - 1) + 62 + 1022;
+  const uint32_t signbit = ((uint32_t)sgn ^ (0u - neg)) & 0x80000000u;
+  prod_to_dd(p, (uint32_t)max(f, 0), signbit, h, l);
+  if (mag == 0 || f < 1) h = l = 0.0;
+}
+
+template <int N>
+__global__ void __launch_bounds__(kBlock, 2) ryser_cplx2_kernel(RyserArgs a) {
+  constexpr int R = (N + 1) / 2;  // rows per lane
+  using Lo = CplxLayout<N>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ CplxShared sh;
+  cplx_stage<N>(static_cast<const double*>(a.A), smem, sh);
+  const longlong2* D = reinterpret_cast<const longlong2*>(smem + Lo::kD);
+  const longlong2* base = reinterpret_cast<const longlong2*>(smem + Lo::kBase);
+  const bool bad = sh.nonfinite || sh.bound_log2 + N > 1000;
+  const bool skip = bad || sh.zero_row;
+  // x_i = Y_i 2^(-s_i - 1).  The padded row of an odd n is 2^60 (a multiplier
+  // of full precision for cprod_mul, which scales by 2^-62 and renormalises),
+  // taken back out of the exponent here.
+  const int eoff = -(sh.sum_s + N) - ((N & 1) ? 60 : 0);
+
+  dd accr = {0.0, 0.0}, acci = {0.0, 0.0};
+  const int lane = threadIdx.x & 31, li = lane & 1;
+  const uint64_t warp_id = (uint64_t)(blockIdx.x * kBlock + threadIdx.x) >> 5;
+  const uint64_t nwarps = (uint64_t)(gridDim.x * kBlock) >> 5;
+  const uint64_t ngroups = skip ? 0 : (a.nchunks + 15) / 16;  // 16 chunks per warp
+  const uint32_t nsteps = 1u << a.c;
+
+  for (uint64_t q = warp_id; q < ngroups; q += nwarps) {
+    const uint64_t kk = q * 16 + (lane >> 1);
+    const bool active = kk < a.nchunks;
+    const uint64_t k = a.k_begin + kk;
+    const uint64_t g0 = k << a.c;
+    uint32_t tlo, tcnt;
+    chunk_window(a, g0, active, tlo, tcnt);
+    const uint32_t kb = (uint32_t)(k & 1u) << a.c;
+    const uint32_t gpar = (uint32_t)(g0 & 1u);
+
+    long long Yr[R], Yi[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int i = li * R + r;
+      const longlong2 b = i < N ? base[i] : make_longlong2(1ll << 60, 0);
+      Yr[r] = b.x;
+      Yi[r] = b.y;
+    }
+    const uint64_t G = gray64(g0);
+    for (int j = (a.c > 0 ? a.c - 1 : 0); j < N - 1; ++j) {
+      const long long msk = -(long long)((G >> j) & 1u);
+      const longlong2* col = D + (size_t)(2 * j) * N + li * R;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        if (li * R + r < N) {
+          Yr[r] += col[r].x & msk;
+          Yi[r] += col[r].y & msk;
+        }
+      }
+    }
+
+    CTerm keep = {0, 0, 0u, 0u, 0};
+    uint32_t kneg = 0u;
+    for (uint32_t t = 0; t < nsteps; ++t) {
+      if (t) {
+        const int j = __ffs(t) - 1;
+        const uint32_t sb = ((t | kb) >> (j + 1)) & 1u;
+        const longlong2* col = D + (size_t)(2 * j + sb) * N + li * R;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          if (li * R + r < N) {
+            const longlong2 d = col[r];
+            Yr[r] += d.x;
+            Yi[r] += d.y;
+          }
+        }
+      }
+      CProd p;
+      cprod_init(p);
+      int ssum = 0;
+#pragma unroll
+      for (int r = 0; r < R; ++r) ssum += cprod_mul(p, Yr[r], Yi[r]);
+      CTerm v{p.r1, p.i1, p.r0, p.i0, -60 + 62 * R - ssum};
+      const CTerm o{__shfl_xor_sync(0xffffffffu, v.r1, 1), __shfl_xor_sync(0xffffffffu, v.i1, 1),
+                    __shfl_xor_sync(0xffffffffu, v.r0, 1), __shfl_xor_sync(0xffffffffu, v.i0, 1),
+                    __shfl_xor_sync(0xffffffffu, v.e, 1)};
+      v = cterm_mul(li ? o : v, li ? v : o);  // both lanes: (lane 0 half) x (lane 1 half)
+      if ((t & 1u) == (uint32_t)li) {
+        keep = v;
+        kneg = (t ^ gpar) & 1u;
+      }
+      if ((t & 1u) || t + 1 == nsteps) {
+        const uint32_t tk = (t & ~1u) + (uint32_t)li;  // the step this lane kept
+        const bool in = tk <= t && tk - tlo < tcnt;
+        const long long zr = ((long long)keep.r1 << 31) | keep.r0;
+        const long long zi = ((long long)keep.i1 << 31) | keep.i0;
+        double hr, lr, hi_, li_;
+        cpart_to_dd(zr, keep.e + eoff, kneg, hr, lr);
+        cpart_to_dd(zi, keep.e + eoff, kneg, hi_, li_);
+        dd_acc(accr, in ? hr : 0.0, in ? lr : 0.0);
+        dd_acc(acci, in ? hi_ : 0.0, in ? li_ : 0.0);
+      }
     }
     accr = dd_make(accr.hi, accr.lo);
     acci = dd_make(acci.hi, acci.lo);

@@ -6,7 +6,9 @@ namespace permgpu {
 
 template <int N>
 static KernelEntry cplx_lo_make() {
-  return {reinterpret_cast<const void*>(&ryser_cplx_kernel<N>), CplxLayout<N>::kBytes};
+  // two lanes per chunk from n = 16 on (register pressure of the complex rows)
+  if (N >= 16) return {reinterpret_cast<const void*>(&ryser_cplx2_kernel<N>), CplxLayout<N>::kBytes, 16};
+  return {reinterpret_cast<const void*>(&ryser_cplx_kernel<N>), CplxLayout<N>::kBytes, 32};
 }
 
 KernelEntry cplx_lo_entry(int n) {

@@ -7,8 +7,9 @@
 namespace permgpu {
 
 struct KernelEntry {
-  const void* fn;  // __global__ function
-  size_t smem;     // dynamic shared memory in bytes
+  const void* fn;          // __global__ function
+  size_t smem;             // dynamic shared memory in bytes
+  int chunks_per_warp = 32;  // chunks one warp walks at a time (lanes per chunk = 32 / this)
 };
 
 KernelEntry real_entry_lo(int n);   // n = 1..24

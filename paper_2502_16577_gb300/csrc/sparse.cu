@@ -12,6 +12,13 @@
 //    reads are broadcasts.
 //  * Every lane counts its zero rows; while the count is positive the term is
 //    exactly zero and the product is skipped.
+//  * Quiet rows.  Inside an aligned block of 2^B steps only the columns with
+//    Gray bits 0..B-1 change, so B sparse columns (their union of rows small,
+//    B in 0..4 from a cost estimate) are moved to those bits (a column
+//    permutation leaves the permanent unchanged).  The rows they do not touch stay
+//    constant for the whole block: their product is formed once per block and
+//    every step multiplies only the touched rows into it (about 2x fewer
+//    products at density 0.2).
 //  * Products, exact per-step double-double accumulation and the fixed-order
 //    reduction are those of the dense real kernel.
 #include <math.h>
@@ -63,6 +70,11 @@ __global__ void __launch_bounds__(kSpBlock) ryser_sparse_kernel(SpArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ SpShared sh;
   __shared__ int s_scale[64];
+  __shared__ int s_cmap[64];            // Gray bit j -> CCS column
+  __shared__ unsigned char s_trow[64];  // rows touched by the columns of bits 0..B-1
+  __shared__ unsigned char s_qrow[64];  // the other (quiet) rows
+  __shared__ int s_nt, s_nq;
+  __shared__ unsigned long long s_tmask;
   const int n = a.n, nnz = a.nnz;
   int32_t* cp = reinterpret_cast<int32_t*>(smem);
   const size_t off_ent = ((sizeof(int32_t) * (n + 1) + 15) / 16) * 16;
@@ -134,9 +146,66 @@ __global__ void __launch_bounds__(kSpBlock) ryser_sparse_kernel(SpArgs a) {
   }
   __syncthreads();
 
+  __shared__ int s_B;
+  if (threadIdx.x == 0) {
+    // Greedily pick up to 4 columns among 0..n-2, each time the one that adds
+    // the fewest rows to the touched set; keep the prefix of B columns that
+    // minimises the products per step, |T| + (n - |T|) / 2^B + 2.  Those
+    // columns take Gray bits 0..B-1 (B <= c); the others keep their order.
+    for (int j = 0; j < 64; ++j) s_cmap[j] = j;
+    int chosen[4] = {-1, -1, -1, -1};
+    unsigned long long masks[5] = {0ull, 0ull, 0ull, 0ull, 0ull};
+    const int bmax = sh.bad ? 0 : min(min(a.c, 4), n - 1);
+    int B = 0;
+    float best_cost = (float)n + 2.0f;
+    for (int b = 0; b < bmax; ++b) {
+      int best = -1, bestc = 1 << 30;
+      for (int j = 0; j < n - 1; ++j) {
+        bool used = false;
+        for (int q = 0; q < b; ++q) used |= chosen[q] == j;
+        if (used) continue;
+        unsigned long long m = masks[b];
+        for (int p = cp[j]; p < cp[j + 1]; ++p) m |= 1ull << ent[p].row;
+        const int cnt = __popcll(m);
+        if (cnt < bestc) bestc = cnt, best = j;
+      }
+      chosen[b] = best;
+      masks[b + 1] = masks[b];
+      for (int p = cp[best]; p < cp[best + 1]; ++p) masks[b + 1] |= 1ull << ent[p].row;
+      const int t_rows = __popcll(masks[b + 1]);
+      const float cost = (float)t_rows + (float)(n - t_rows) / (float)(1 << (b + 1)) + 2.0f;
+      if (cost < best_cost) best_cost = cost, B = b + 1;
+    }
+    const unsigned long long tmask = masks[B];
+    if (B > 0) {
+      int k = 0;
+      for (int b = 0; b < B; ++b) s_cmap[k++] = chosen[b];
+      for (int j = 0; j < n - 1; ++j) {
+        bool used = false;
+        for (int q = 0; q < B; ++q) used |= chosen[q] == j;
+        if (!used) s_cmap[k++] = j;
+      }
+      s_cmap[n - 1] = n - 1;
+    }
+    s_B = B;
+    int nt = 0, nq = 0;
+    for (int i = 0; i < n; ++i) {
+      if ((tmask >> i) & 1ull) s_trow[nt++] = (unsigned char)i;
+      else s_qrow[nq++] = (unsigned char)i;
+    }
+    s_nt = nt;
+    s_nq = nq;
+    s_tmask = tmask;
+  }
+  __syncthreads();
+  const int nt = s_nt, nq = s_nq;
+  const unsigned long long tmask = s_tmask;
+  const uint32_t bmask = (1u << s_B) - 1u;
+
   const bool skip = sh.bad || sh.zero_row || sh.bound_log2 + n > 1000;
-  const int K1 = 64 * n + 1025 - sh.sum_s;
-  const uint32_t one = (uint32_t)a.one;
+  // binary64 exponent of a term: three chains (two over the touched rows, one
+  // over the quiet rows) and two merges; see prod_mul for the bookkeeping
+  const int F0 = 33 * n + 1022 - 56 - sh.sum_s;
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   const uint64_t warp_id = (uint64_t)(blockIdx.x * kSpBlock + tid) >> 5;
@@ -155,33 +224,58 @@ __global__ void __launch_bounds__(kSpBlock) ryser_sparse_kernel(SpArgs a) {
     for (int i = 0; i < n; ++i) xs[i * kSpBlock + tid] = base[i];
     const uint64_t G = gray64(g0);
     for (int j = (a.c > 0 ? a.c - 1 : 0); j < n - 1; ++j) {
-      if ((G >> j) & 1u)
-        for (int p = cp[j]; p < cp[j + 1]; ++p) xs[ent[p].row * kSpBlock + tid] += ent[p].d;
+      if ((G >> j) & 1u) {
+        const int cj = s_cmap[j];
+        for (int p = cp[cj]; p < cp[cj + 1]; ++p) xs[ent[p].row * kSpBlock + tid] += ent[p].d;
+      }
     }
-    int zeros = 0;
-    for (int i = 0; i < n; ++i) zeros += xs[i * kSpBlock + tid] == 0;
+    int zeros = 0, zq = 0;  // zero rows in all / in the quiet rows
+    for (int i = 0; i < n; ++i) {
+      const int z = xs[i * kSpBlock + tid] == 0;
+      zeros += z;
+      zq += ((tmask >> i) & 1ull) ? 0 : z;
+    }
 
+    Prod pq;  // product of the quiet rows of the current block
+    uint32_t negq = 0, eposq = 0;
+    prod_init(pq);
     for (uint32_t t = 0; t < nsteps; ++t) {
       if (t) {
-        const int j = __ffs(t) - 1;
-        const bool leave = ((t | kb) >> (j + 1)) & 1u;
+        const int j = s_cmap[__ffs(t) - 1];
+        const bool leave = ((t | kb) >> __ffs(t)) & 1u;  // bit j + 1 of g
         for (int p = cp[j]; p < cp[j + 1]; ++p) {  // Alg. 2: nonzeros of column j only
           const SpEntry e = ent[p];
           long long* xp = xs + e.row * kSpBlock + tid;
           const long long old = *xp;
           const long long nv = leave ? old - e.d : old + e.d;
           *xp = nv;
-          zeros += (nv == 0) - (old == 0);
+          const int dz = (nv == 0) - (old == 0);
+          zeros += dz;
+          zq += ((tmask >> e.row) & 1ull) ? 0 : dz;
+        }
+      }
+      if ((t & bmask) == 0u) {
+        // a new block: the quiet rows are constant until its end
+        prod_init(pq);
+        negq = 0;
+        eposq = 0;
+        // (skipped while a quiet row is zero: then every term of the block is)
+        for (int k = 0; k < (zq == 0 ? nq : 0); ++k) {
+          const long long ya = xs[s_qrow[k] * kSpBlock + tid];
+          const uint32_t ma = (uint32_t)(ya >> 63);
+          const unsigned long long aa = (unsigned long long)((ya ^ (long long)(int32_t)ma) - (long long)(int32_t)ma);
+          negq += ma;
+          eposq += prod_mul(pq, (uint32_t)aa, (uint32_t)(aa >> 32));
         }
       }
       if (zeros == 0 && active) {
         Prod pa, pb;
         prod_init(pa);
         prod_init(pb);
-        uint32_t neg = 0, epos = 0;
-        int i = 0;
-        for (; i + 1 < n; i += 2) {
-          const long long ya = xs[i * kSpBlock + tid], yb = xs[(i + 1) * kSpBlock + tid];
+        uint32_t neg = negq, epos = eposq;
+        int k = 0;
+        for (; k + 1 < nt; k += 2) {
+          const long long ya = xs[s_trow[k] * kSpBlock + tid], yb = xs[s_trow[k + 1] * kSpBlock + tid];
           const uint32_t ma = (uint32_t)(ya >> 63), mb = (uint32_t)(yb >> 63);
           const unsigned long long aa = (unsigned long long)((ya ^ (long long)(int32_t)ma) - (long long)(int32_t)ma);
           const unsigned long long ab = (unsigned long long)((yb ^ (long long)(int32_t)mb) - (long long)(int32_t)mb);
@@ -189,16 +283,16 @@ __global__ void __launch_bounds__(kSpBlock) ryser_sparse_kernel(SpArgs a) {
           epos += prod_mul(pa, (uint32_t)aa, (uint32_t)(aa >> 32));
           epos += prod_mul(pb, (uint32_t)ab, (uint32_t)(ab >> 32));
         }
-        if (i < n) {
-          const long long ya = xs[i * kSpBlock + tid];
+        if (k < nt) {
+          const long long ya = xs[s_trow[k] * kSpBlock + tid];
           const uint32_t ma = (uint32_t)(ya >> 63);
           const unsigned long long aa = (unsigned long long)((ya ^ (long long)(int32_t)ma) - (long long)(int32_t)ma);
           neg += ma;
           epos += prod_mul(pa, (uint32_t)aa, (uint32_t)(aa >> 32));
         }
         epos += prod_mul(pa, pb.m0, pb.m1);
-        const int shifts = 30 * (n + 1) - (int)epos;
-        const int f = K1 - shifts - (n + 1);
+        epos += prod_mul(pa, pq.m0, pq.m1);
+        const int f = F0 + (int)epos;
         const uint32_t signbit = (neg ^ t ^ gpar) << 31;
         double th, tl;
         prod_to_dd(pa, (uint32_t)max(f, 0), signbit, th, tl);

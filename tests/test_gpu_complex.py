@@ -42,7 +42,7 @@ def test_small_vs_bruteforce(pg, oracle, n):
         assert abs(got.imag - float(im)) <= 1e-14 * scale
 
 
-@pytest.mark.parametrize("n", [9, 12, 16, 20])
+@pytest.mark.parametrize("n", [9, 12, 15, 16, 17, 19, 20, 21])
 def test_unitary_vs_dp(pg, oracle, n):
     U = syn.haar_unitary(n, 8100 + n)
     want = oracle.perm_dp_c128(U)
