@@ -290,7 +290,8 @@ __device__ __forceinline__ void batch_item_real(const BatchArgs& a, const BatchI
     const int m = a.lane_mats[it.mat + (active ? lane : 0)];
     const BatchMat bm = a.mats[m];
     const bool ok = active && bm.flags == 0;
-    batch_sweep_real<K>(reinterpret_cast<const long long*>(a.table + bm.d_off), bm.sum_s, K - 1, 0ull, ok, acc);
+    if constexpr (K <= 16)  // one matrix per lane only for short sweeps (as complex)
+      batch_sweep_real<K>(reinterpret_cast<const long long*>(a.table + bm.d_off), bm.sum_s, K - 1, 0ull, ok, acc);
     if (active) {
       a.slots[2 * bm.slot0] = acc;
       a.slots[2 * bm.slot0 + 1] = zero;
@@ -310,6 +311,85 @@ __device__ __forceinline__ void batch_item_real(const BatchArgs& a, const BatchI
   }
 }
 
+// Chunked sweep of a K x K complex matrix (K >= 16) by a lane pair, as in
+// ryser_cplx2_kernel: lane li of the pair holds rows li R .. li R + R - 1,
+// one shuffle and one complex multiply combine the halves, each lane adds the
+// terms of every second step.
+template <int K>
+__device__ __forceinline__ void batch_sweep2(const longlong2* __restrict__ D, int sum_s, int c, uint64_t g0,
+                                             bool active, dd& accr, dd& acci) {
+  constexpr int R = (K + 1) / 2;
+  const int li = threadIdx.x & 1;
+  const longlong2* base = D + (size_t)2 * (K - 1) * K;
+  const int eoff = -(sum_s + K) - ((K & 1) ? 60 : 0);
+  const uint32_t nsteps = 1u << c;
+  const uint32_t kb = (uint32_t)((g0 >> c) & 1u) << c;
+  const uint32_t gpar = (uint32_t)(g0 & 1u);
+  long long Yr[R], Yi[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int i = li * R + r;
+    const longlong2 b = i < K ? __ldg(base + i) : make_longlong2(1ll << 60, 0);
+    Yr[r] = b.x;
+    Yi[r] = b.y;
+  }
+  const uint64_t G = gray64(g0);
+  for (int j = (c > 0 ? c - 1 : 0); j < K - 1; ++j) {
+    const long long msk = -(long long)((G >> j) & 1u);
+    const longlong2* col = D + (size_t)(2 * j) * K + li * R;
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+      if (li * R + r < K) {
+        const longlong2 d = __ldg(col + r);
+        Yr[r] += d.x & msk;
+        Yi[r] += d.y & msk;
+      }
+  }
+  CTerm keep = {0, 0, 0u, 0u, 0};
+  uint32_t kneg = 0u;
+  for (uint32_t t = 0; t < nsteps; ++t) {
+    if (t) {
+      const int j = __ffs(t) - 1;
+      const uint32_t sb = ((t | kb) >> (j + 1)) & 1u;
+      const longlong2* col = D + (size_t)(2 * j + sb) * K + li * R;
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+        if (li * R + r < K) {
+          const longlong2 d = __ldg(col + r);
+          Yr[r] += d.x;
+          Yi[r] += d.y;
+        }
+    }
+    CProd p;
+    cprod_init(p);
+    int ssum = 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) ssum += cprod_mul(p, Yr[r], Yi[r]);
+    CTerm v{p.r1, p.i1, p.r0, p.i0, -60 + 62 * R - ssum};
+    const CTerm o{__shfl_xor_sync(0xffffffffu, v.r1, 1), __shfl_xor_sync(0xffffffffu, v.i1, 1),
+                  __shfl_xor_sync(0xffffffffu, v.r0, 1), __shfl_xor_sync(0xffffffffu, v.i0, 1),
+                  __shfl_xor_sync(0xffffffffu, v.e, 1)};
+    v = cterm_mul(li ? o : v, li ? v : o);
+    if ((t & 1u) == (uint32_t)li) {
+      keep = v;
+      kneg = (t ^ gpar) & 1u;
+    }
+    if ((t & 1u) || t + 1 == nsteps) {
+      const uint32_t tk = (t & ~1u) + (uint32_t)li;
+      const bool in = active && tk <= t;
+      const long long zr = ((long long)keep.r1 << 31) | keep.r0;
+      const long long zi = ((long long)keep.i1 << 31) | keep.i0;
+      double hr, lr, hi_, li_;
+      cpart_to_dd(zr, keep.e + eoff, kneg, hr, lr);
+      cpart_to_dd(zi, keep.e + eoff, kneg, hi_, li_);
+      dd_acc(accr, in ? hr : 0.0, in ? lr : 0.0);
+      dd_acc(acci, in ? hi_ : 0.0, in ? li_ : 0.0);
+    }
+  }
+  accr = dd_make(accr.hi, accr.lo);
+  acci = dd_make(acci.hi, acci.lo);
+}
+
 template <int K>
 __device__ __forceinline__ void batch_item(const BatchArgs& a, const BatchItem& it) {
   const int lane = threadIdx.x & 31;
@@ -319,17 +399,23 @@ __device__ __forceinline__ void batch_item(const BatchArgs& a, const BatchItem& 
     const int m = a.lane_mats[it.mat + (active ? lane : 0)];
     const BatchMat bm = a.mats[m];
     const bool ok = active && bm.flags == 0;
-    batch_sweep<K>(a.table + bm.d_off, bm.sum_s, K - 1, 0ull, ok, accr, acci);
+    // one complex matrix per lane only for short sweeps (K <= 16, enforced by
+    // the plan): longer rows would not fit the registers of a lane
+    if constexpr (K <= 16) batch_sweep<K>(a.table + bm.d_off, bm.sum_s, K - 1, 0ull, ok, accr, acci);
     if (active) {
       a.slots[2 * bm.slot0] = accr;
       a.slots[2 * bm.slot0 + 1] = acci;
     }
   } else {
     const BatchMat bm = a.mats[it.mat];
-    const uint64_t chunk = (uint64_t)it.chunk0 + lane;
+    const uint64_t chunk = (uint64_t)it.chunk0 + (K >= 16 ? (lane >> 1) : lane);
     const uint64_t nchunks = 1ull << (K - 1 - it.c);
     const bool active = chunk < nchunks && bm.flags == 0;
-    batch_sweep<K>(a.table + bm.d_off, bm.sum_s, it.c, (active ? chunk : 0ull) << it.c, active, accr, acci);
+    if constexpr (K >= 16)
+      batch_sweep2<K>(a.table + bm.d_off, bm.sum_s, it.c, (active ? chunk : 0ull) << it.c, active, accr, acci);
+    else
+      batch_sweep<(K < 16 ? K : 1)>(a.table + bm.d_off, bm.sum_s, it.c, (active ? chunk : 0ull) << it.c, active,
+                                    accr, acci);
     accr = dd_warp_sum(accr);
     acci = dd_warp_sum(acci);
     if (lane == 0) {
@@ -339,7 +425,10 @@ __device__ __forceinline__ void batch_item(const BatchArgs& a, const BatchItem& 
   }
 }
 
-__global__ void __launch_bounds__(kBlock, 1) batch_main_kernel(BatchArgs a) {
+// One persistent kernel per element type (each is register-bounded for 2 CTAs
+// per SM on its own).
+template <bool REAL>
+__global__ void __launch_bounds__(kBlock, 2) batch_main_kernel(BatchArgs a) {
   const int lane = threadIdx.x & 31;
   for (;;) {
     int idx = 0;
@@ -350,7 +439,7 @@ __global__ void __launch_bounds__(kBlock, 1) batch_main_kernel(BatchArgs a) {
     switch (it.k) {
 #define PERM_BATCH_CASE(KK)       \
   case KK:                        \
-    if (a.type == PERM_F64)       \
+    if constexpr (REAL)           \
       batch_item_real<KK>(a, it); \
     else                          \
       batch_item<KK>(a, it);      \
@@ -516,15 +605,17 @@ static int batch_build(perm_batch_plan* p) {
     } else {
       const int c = p->cls_c[k];
       const uint64_t nchunks = 1ull << (k - 1 - c);
+      // complex k >= 16: lane pairs, 16 chunks per warp item
+      const uint64_t per_item = (p->type == PERM_C128 && k >= 16) ? 16 : 32;
       for (int m : ms) {
         mats[m].slot0 = slot;
-        for (uint64_t ch = 0; ch < nchunks; ch += 32) {
+        for (uint64_t ch = 0; ch < nchunks; ch += per_item) {
           BatchItem it;
           memset(&it, 0, sizeof(it));
           it.mode = kWarpMode;
           it.k = k;
           it.c = c;
-          it.count = 32;
+          it.count = (int)per_item;
           it.mat = m;
           it.slot = slot++;
           it.chunk0 = (int64_t)ch;
@@ -606,11 +697,16 @@ static int batch_enqueue(const perm_batch_plan* p, cudaStream_t s) {
   if (cudaMemsetAsync(p->d_counter, 0, sizeof(unsigned int), s) != cudaSuccess) return PERM_ECUDA;
   batch_prep_kernel<<<p->count, kBlock, 0, s>>>(a);
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_main_kernel, kBlock, 0) != cudaSuccess || nb < 1)
-    nb = 1;
+  const bool real = p->type == PERM_F64;
+  const void* mk = real ? reinterpret_cast<const void*>(batch_main_kernel<true>)
+                        : reinterpret_cast<const void*>(batch_main_kernel<false>);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, mk, kBlock, 0) != cudaSuccess || nb < 1) nb = 1;
   int want = (p->nitems + kWarps - 1) / kWarps;
   int grid = std::max(1, std::min(p->sms * nb, want));
-  batch_main_kernel<<<grid, kBlock, 0, s>>>(a);
+  if (real)
+    batch_main_kernel<true><<<grid, kBlock, 0, s>>>(a);
+  else
+    batch_main_kernel<false><<<grid, kBlock, 0, s>>>(a);
   batch_finish_kernel<<<(p->count + 127) / 128, 128, 0, s>>>(a, p->d_nslots);
   return cudaGetLastError() == cudaSuccess ? PERM_OK : PERM_ECUDA;
 }
@@ -705,7 +801,7 @@ extern "C" int perm_batched_autotune(perm_batch_plan* plan, int rounds, void* st
     std::vector<Cand> cands;
     if (k <= 16) cands.push_back({kLaneMode, k - 1});
     for (int c = std::max(2, k - 1 - 12); c <= k - 1 - 5; ++c) cands.push_back({kWarpMode, c});
-    if (cands.empty()) cands.push_back({kLaneMode, k - 1});
+    if (cands.empty()) cands.push_back({k <= 16 ? kLaneMode : kWarpMode, k <= 16 ? k - 1 : std::max(0, k - 6)});
     float best = 1e30f;
     Cand pick = {plan->cls_mode[k], plan->cls_c[k]};
     for (const Cand& cd : cands) {
