@@ -58,7 +58,8 @@ typedef enum {
                          binary64 result that can overflow                      */
   PERM_EOVERFLOW = 3, /* BIN: the permanent may not fit 128 bits              */
   PERM_ECUDA = 4,     /* a CUDA call failed                                    */
-  PERM_ENOMEM = 5     /* scratch allocation failed                             */
+  PERM_ENOMEM = 5,    /* scratch allocation failed                             */
+  PERM_EABORTED = 6   /* stopped early by the word of perm_set_abort_word      */
 } perm_status_t;
 
 /*
@@ -274,6 +275,24 @@ int perm_f64_noalloc(const double* A, int n, double* out, int32_t* status, void*
  *   out  host double[count], 1 <= count <= 5.  Waits for the stream.
  */
 int perm_pipe_peaks(double* out, int count, void* stream);
+
+/*
+ * Cancellation (no counterpart in the paper; a service around Alg. 3's chunk
+ * loop).  perm_set_abort_word registers a word of page-locked MAPPED host
+ * memory (cudaHostAlloc with cudaHostAllocMapped, or perm_abort_word_alloc);
+ * NULL unregisters it.  The sweeps of perm, perm_range, perm_sparse and
+ * perm_f64_noalloc launched afterwards read it once per chunk group and warp;
+ * when it is nonzero they stop and report PERM_EABORTED (out NaN, or zero for
+ * 0/1).  Setting the word to nonzero from the host while a launch runs ends
+ * that launch early.  Nothing waits on the word.  Returns PERM_EINVAL when
+ * the pointer is not mapped host memory.  One word for the process; the
+ * batched and gradient launches do not read it.
+ * perm_abort_word_alloc / perm_abort_word_free - allocate (zeroed) / free
+ * such a word (freeing the registered word unregisters it).
+ */
+int perm_set_abort_word(volatile uint32_t* host_mapped);
+int perm_abort_word_alloc(volatile uint32_t** host_word);
+int perm_abort_word_free(volatile uint32_t* host_word);
 
 /* Human-readable name of a perm_status_t; never NULL. */
 const char* perm_status_string(int status);

@@ -19,10 +19,10 @@ import ctypes
 import numpy as np
 
 from . import _lib
-from ._lib import PERM_BIN, PERM_C128, PERM_F64, PermError, check, load
+from ._lib import PERM_BIN, PERM_C128, PERM_EABORTED, PERM_F64, PermError, check, load
 
-__all__ = ["perm", "perm_async", "perm_range", "perm_range_async", "perm_combine", "perm_sparse", "perm_sparse_async", "perm_host", "pipe_peaks", "BatchPlan", "perm_grad", "perm_grad_async", "perm_grad_batched", "perm_grad_batched_async", "permanent", "perm_type_of", "PermError",
-           "PERM_F64", "PERM_C128", "PERM_BIN", "load"]
+__all__ = ["perm", "perm_async", "perm_range", "perm_range_async", "perm_combine", "perm_sparse", "perm_sparse_async", "perm_host", "pipe_peaks", "BatchPlan", "AbortWord", "perm_grad", "perm_grad_async", "perm_grad_batched", "perm_grad_batched_async", "permanent", "perm_type_of", "PermError",
+           "PERM_F64", "PERM_C128", "PERM_BIN", "PERM_EABORTED", "load"]
 
 
 def _torch():
@@ -310,6 +310,29 @@ def permanent(A):
     if _PERMANENT is None:
         _PERMANENT = _autograd_function()
     return _PERMANENT.apply(A)
+
+
+class AbortWord:
+    """A word of mapped host memory registered with perm_set_abort_word: set()
+    makes the sweeps of perm / perm_range / perm_sparse stop at their next
+    chunk group with PERM_EABORTED; clear() lets new launches run."""
+
+    def __init__(self):
+        lib = load()
+        self._p = ctypes.POINTER(ctypes.c_uint32)()
+        check(lib.perm_abort_word_alloc(ctypes.byref(self._p)), "perm_abort_word_alloc")
+        check(lib.perm_set_abort_word(ctypes.cast(self._p, ctypes.c_void_p)), "perm_set_abort_word")
+
+    def set(self) -> None:
+        self._p[0] = 1
+
+    def clear(self) -> None:
+        self._p[0] = 0
+
+    def close(self) -> None:
+        if self._p:
+            load().perm_abort_word_free(self._p)
+            self._p = ctypes.POINTER(ctypes.c_uint32)()
 
 
 class BatchPlan:

@@ -11,7 +11,7 @@ import os
 from . import build as _build
 
 PERM_F64, PERM_C128, PERM_BIN = 0, 1, 2
-PERM_OK, PERM_EINVAL, PERM_ERANGE, PERM_EOVERFLOW, PERM_ECUDA, PERM_ENOMEM = range(6)
+PERM_OK, PERM_EINVAL, PERM_ERANGE, PERM_EOVERFLOW, PERM_ECUDA, PERM_ENOMEM, PERM_EABORTED = range(7)
 
 _vp = ctypes.c_void_p
 _i32p = ctypes.POINTER(ctypes.c_int32)
@@ -21,6 +21,7 @@ SYMBOLS = ("perm", "perm_range", "perm_combine", "perm_sparse", "perm_host", "pe
            "perm_batched_plan_create", "perm_batched", "perm_batched_autotune", "perm_batched_plan_info",
            "perm_batched_plan_destroy", "perm_grad", "perm_grad_batched", "perm_decomp_create", "perm_decomp_info", "perm_decomp_leaf",
            "perm_decomp_filtered", "perm_decomp_eval", "perm_decomp_destroy", "perm_sparse_decomp",
+           "perm_set_abort_word", "perm_abort_word_alloc", "perm_abort_word_free",
            "perm_status_string", "perm_abi_version")
 
 
@@ -93,6 +94,12 @@ def load(build_if_missing: bool = False):
     lib.perm_sparse_decomp.restype = ctypes.c_int
     lib.perm_sparse_decomp.argtypes = [ctypes.c_int, _vp, _vp, _vp, ctypes.c_int64, _dp, ctypes.POINTER(DecompInfo),
                                        _vp]
+    lib.perm_set_abort_word.restype = ctypes.c_int
+    lib.perm_set_abort_word.argtypes = [_vp]
+    lib.perm_abort_word_alloc.restype = ctypes.c_int
+    lib.perm_abort_word_alloc.argtypes = [ctypes.POINTER(ctypes.POINTER(ctypes.c_uint32))]
+    lib.perm_abort_word_free.restype = ctypes.c_int
+    lib.perm_abort_word_free.argtypes = [ctypes.POINTER(ctypes.c_uint32)]
     lib.perm_host.restype = ctypes.c_int
     lib.perm_host.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp]
     lib.perm_pipe_peaks.restype = ctypes.c_int

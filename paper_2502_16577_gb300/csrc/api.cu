@@ -4,6 +4,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <atomic>
 #include <mutex>
 
 #include "common.cuh"
@@ -66,6 +67,12 @@ static int floor_log2_u64(uint64_t v) {
 // least 64 warp-groups of 32 chunks per resident warp (tail below ~1.6%), but
 // keep 2^c >= 4n so that starting a chunk (at most n(n-c) adds) stays small
 // against its 2^c steps of n multiplies.
+// ------------------------------------------------------------ cancellation
+
+static std::atomic<const volatile uint32_t*> g_abort_word{nullptr};
+
+const volatile uint32_t* current_abort_word() { return g_abort_word.load(std::memory_order_acquire); }
+
 int plan_chunk_exponent(int n, uint64_t nsteps, int warps_resident) {
   int cmax = n - 1 < 30 ? n - 1 : 30;
   if (cmax < 0) cmax = 0;
@@ -105,7 +112,7 @@ static int launch_ryser(const KernelEntry& ke, const void* A, int n, uint64_t g_
     return PERM_ENOMEM;
   }
   unsigned int* counter = reinterpret_cast<unsigned int*>(static_cast<char*>(ws) + part_bytes * (size_t)grid);
-  if (cudaMemsetAsync(counter, 0, sizeof(unsigned int), s) != cudaSuccess) {
+  if (cudaMemsetAsync(counter, 0, 2 * sizeof(unsigned int), s) != cudaSuccess) {
     cudaFreeAsync(ws, s);
     return PERM_ECUDA;
   }
@@ -124,6 +131,8 @@ static int launch_ryser(const KernelEntry& ke, const void* A, int n, uint64_t g_
   args.counter = counter;
   args.out = out;
   args.status = status;
+  args.abort_word = current_abort_word();
+  args.aborted = counter + 1;
   void* params[] = {&args};
   cudaError_t e = cudaLaunchKernel(ke.fn, dim3(grid), dim3(kBlock), params, ke.smem, s);
   cudaError_t f = cudaFreeAsync(ws, s);
@@ -214,6 +223,43 @@ extern "C" {
 
 int perm_abi_version(void) { return PERM_ABI_VERSION; }
 
+int perm_set_abort_word(volatile uint32_t* host_mapped) {
+  if (!host_mapped) {
+    g_abort_word.store(nullptr, std::memory_order_release);
+    return PERM_OK;
+  }
+  void* dev = nullptr;
+  if (cudaHostGetDevicePointer(&dev, const_cast<uint32_t*>(host_mapped), 0) != cudaSuccess) {
+    cudaGetLastError();
+    return PERM_EINVAL;  // not page-locked mapped host memory
+  }
+  g_abort_word.store(static_cast<const volatile uint32_t*>(dev), std::memory_order_release);
+  return PERM_OK;
+}
+
+int perm_abort_word_alloc(volatile uint32_t** host_word) {
+  if (!host_word) return PERM_EINVAL;
+  void* p = nullptr;
+  if (cudaHostAlloc(&p, sizeof(uint32_t), cudaHostAllocMapped) != cudaSuccess) {
+    cudaGetLastError();
+    return PERM_ENOMEM;
+  }
+  *static_cast<volatile uint32_t*>(p) = 0u;
+  *host_word = static_cast<volatile uint32_t*>(p);
+  return PERM_OK;
+}
+
+int perm_abort_word_free(volatile uint32_t* host_word) {
+  if (!host_word) return PERM_OK;
+  if (g_abort_word.load() != nullptr) {
+    void* dev = nullptr;
+    if (cudaHostGetDevicePointer(&dev, const_cast<uint32_t*>(host_word), 0) == cudaSuccess &&
+        dev == (const void*)g_abort_word.load())
+      g_abort_word.store(nullptr);
+  }
+  return cudaFreeHost(const_cast<uint32_t*>(host_word)) == cudaSuccess ? PERM_OK : PERM_ECUDA;
+}
+
 const char* perm_status_string(int status) {
   switch (status) {
     case PERM_OK: return "PERM_OK";
@@ -222,6 +268,7 @@ const char* perm_status_string(int status) {
     case PERM_EOVERFLOW: return "PERM_EOVERFLOW: the permanent may not fit the output";
     case PERM_ECUDA: return "PERM_ECUDA: a CUDA call failed";
     case PERM_ENOMEM: return "PERM_ENOMEM: scratch allocation failed";
+    case PERM_EABORTED: return "PERM_EABORTED: stopped by the registered abort word";
     default: return "unknown perm status";
   }
 }

@@ -181,6 +181,7 @@ __global__ void __launch_bounds__(kBlock, 2) ryser_bin_kernel(RyserArgs a) {
   const uint32_t nsteps = 1u << a.c;
 
   for (uint64_t q = warp_id; q < ngroups; q += nwarps) {
+    if (should_abort(a.abort_word, a.aborted)) break;
     const uint64_t kk = q * 32 + lane;
     const bool active = kk < a.nchunks;
     const uint64_t k = a.k_begin + kk;
@@ -260,13 +261,16 @@ __global__ void __launch_bounds__(kBlock, 2) ryser_bin_kernel(RyserArgs a) {
     // sign-extend a 160-bit residue to 192 bits: the true sum fits W bits
     if (L == 5) tot[5] = (tot[4] & 0x80000000u) ? 0xFFFFFFFFu : 0u;
     int32_t st = PERM_OK;
+    const bool aborted = *a.aborted != 0u;
     if (sh.bad_entry) st = PERM_EINVAL;
+    else if (aborted) st = PERM_EABORTED;
     else if (!sh.zero_row && sh.bound_log2 >= (float)(32 * L - N + 1) - 0.01f) st = PERM_EOVERFLOW;
     uint64_t* out = static_cast<uint64_t*>(a.out);
     if (a.mode == 1) {
-      out[0] = sh.bad_entry ? 0ull : ((uint64_t)tot[1] << 32) | tot[0];
-      out[1] = sh.bad_entry ? 0ull : ((uint64_t)tot[3] << 32) | tot[2];
-      out[2] = sh.bad_entry ? 0ull : ((uint64_t)tot[5] << 32) | tot[4];
+      const bool none = sh.bad_entry || aborted;
+      out[0] = none ? 0ull : ((uint64_t)tot[1] << 32) | tot[0];
+      out[1] = none ? 0ull : ((uint64_t)tot[3] << 32) | tot[2];
+      out[2] = none ? 0ull : ((uint64_t)tot[5] << 32) | tot[4];
     } else {
       // sum = (-1)^(n-1) 2^(n-1) perm  (mod 2^W)
       uint32_t v[6];

@@ -87,7 +87,22 @@ struct RyserArgs {
   unsigned int* counter;  // arrival counter (scratch, zero before launch)
   void* out;
   int32_t* status;    // optional device status word
+  const volatile uint32_t* abort_word;  // device view of a host-mapped word, or null
+  unsigned int* aborted;                // scratch word next to the counter (zeroed)
 };
+
+// Cancellation between chunk groups (perm_set_abort_word): lane 0 reads the
+// host-mapped word once per group and the warp follows it; a warp that stops
+// marks the launch so that the last CTA reports PERM_EABORTED.  No waiting.
+__device__ __forceinline__ bool should_abort(const volatile uint32_t* word, unsigned int* flag) {
+  if (!word) return false;
+  uint32_t v = 0u;
+  if ((threadIdx.x & 31) == 0) v = *word;
+  v = __shfl_sync(0xffffffffu, v, 0);
+  if (v == 0u) return false;
+  if ((threadIdx.x & 31) == 0) atomicOr(flag, 1u);
+  return true;
+}
 
 // Gray code of step g (Sec. 2): bit j set <=> column j is in the subset.
 __device__ __forceinline__ uint64_t gray64(uint64_t g) { return g ^ (g >> 1); }

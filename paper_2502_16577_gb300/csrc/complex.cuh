@@ -150,6 +150,7 @@ __global__ void __launch_bounds__(kBlock, (N <= 8 ? 2 : 1)) ryser_cplx_kernel(Ry
   const uint32_t nsteps = 1u << a.c;
 
   for (uint64_t q = warp_id; q < ngroups; q += nwarps) {
+    if (should_abort(a.abort_word, a.aborted)) break;
     const uint64_t kk = q * 32 + lane;
     const bool active = kk < a.nchunks;
     const uint64_t k = a.k_begin + kk;
@@ -238,6 +239,7 @@ __global__ void __launch_bounds__(kBlock, (N <= 8 ? 2 : 1)) ryser_cplx_kernel(Ry
       int32_t st = PERM_OK;
       if (sh.nonfinite) st = PERM_EINVAL;
       else if (sh.bound_log2 + N > 1000) st = PERM_ERANGE;
+      else if (*a.aborted) st = PERM_EABORTED;
       const double nan = __longlong_as_double(0x7ff8000000000000ll);
       if (a.mode == 0) {
         const double f = (N & 1) ? 2.0 : -2.0;
@@ -324,6 +326,7 @@ __global__ void __launch_bounds__(kBlock, 2) ryser_cplx2_kernel(RyserArgs a) {
   const uint32_t nsteps = 1u << a.c;
 
   for (uint64_t q = warp_id; q < ngroups; q += nwarps) {
+    if (should_abort(a.abort_word, a.aborted)) break;
     const uint64_t kk = q * 16 + (lane >> 1);
     const bool active = kk < a.nchunks;
     const uint64_t k = a.k_begin + kk;
@@ -421,6 +424,7 @@ __global__ void __launch_bounds__(kBlock, 2) ryser_cplx2_kernel(RyserArgs a) {
       int32_t st = PERM_OK;
       if (sh.nonfinite) st = PERM_EINVAL;
       else if (sh.bound_log2 + N > 1000) st = PERM_ERANGE;
+      else if (*a.aborted) st = PERM_EABORTED;
       const double nan = __longlong_as_double(0x7ff8000000000000ll);
       if (a.mode == 0) {
         const double f = (N & 1) ? 2.0 : -2.0;

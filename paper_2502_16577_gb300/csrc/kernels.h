@@ -20,6 +20,9 @@ KernelEntry bin_hi_entry(int n);    // n = 33..63
 KernelEntry cplx_lo_entry(int n);   // n = 1..24
 KernelEntry cplx_hi_entry(int n);   // n = 25..63
 
+// Device view of the word registered with perm_set_abort_word, or null (api.cu).
+const volatile uint32_t* current_abort_word();
+
 // Chunk exponent of a launch over nsteps Gray steps (api.cu).
 int plan_chunk_exponent(int n, uint64_t nsteps, int warps_resident);
 

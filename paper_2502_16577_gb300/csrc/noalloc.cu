@@ -98,9 +98,9 @@ extern "C" int perm_f64_noalloc(const double* A, int n, double* out, int32_t* st
   const int grid = (int)(need < (uint64_t)grid_full ? (need > 0 ? need : 1) : grid_full);
   // the fixed array must hold one partial per CTA and the counter
   const size_t part_bytes = sizeof(dd) * (size_t)grid;
-  if (part_bytes + sizeof(unsigned int) > kNoAllocScratchBytes) return PERM_ENOMEM;
+  if (part_bytes + 2 * sizeof(unsigned int) > kNoAllocScratchBytes) return PERM_ENOMEM;
   unsigned int* counter = reinterpret_cast<unsigned int*>(static_cast<char*>(nd.scratch) + part_bytes);
-  if (cudaMemsetAsync(counter, 0, sizeof(unsigned int), s) != cudaSuccess) return PERM_ECUDA;
+  if (cudaMemsetAsync(counter, 0, 2 * sizeof(unsigned int), s) != cudaSuccess) return PERM_ECUDA;
   RyserArgs args;
   memset(&args, 0, sizeof(args));
   args.A = A;
@@ -116,6 +116,8 @@ extern "C" int perm_f64_noalloc(const double* A, int n, double* out, int32_t* st
   args.counter = counter;
   args.out = out;
   args.status = status;
+  args.abort_word = current_abort_word();
+  args.aborted = counter + 1;
   void* params[] = {&args};
   if (cudaLaunchKernel(ke.fn, dim3(grid), dim3(kBlock), params, ke.smem, s) != cudaSuccess) {
     cudaGetLastError();

@@ -205,6 +205,7 @@ __global__ void __launch_bounds__(kBlock, (N <= 48 ? 2 : 1)) ryser_real_kernel(R
   const uint32_t nsteps = 1u << a.c;
 
   for (uint64_t q = warp_id; q < ngroups; q += nwarps) {
+    if (should_abort(a.abort_word, a.aborted)) break;
     const uint64_t kk = q * 32 + lane;
     const bool active = kk < a.nchunks;
     const uint64_t k = a.k_begin + kk;
@@ -277,6 +278,7 @@ __global__ void __launch_bounds__(kBlock, (N <= 48 ? 2 : 1)) ryser_real_kernel(R
       int32_t st = PERM_OK;
       if (sh.nonfinite) st = PERM_EINVAL;
       else if (sh.bound_log2 + N > 1000) st = PERM_ERANGE;
+      else if (*a.aborted) st = PERM_EABORTED;
       if (a.mode == 0) {
         const double f = (N & 1) ? 2.0 : -2.0;  // 4 (n mod 2) - 2
         out[0] = st != PERM_OK ? __longlong_as_double(0x7ff8000000000000ll)
