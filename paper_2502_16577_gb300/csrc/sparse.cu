@@ -19,11 +19,8 @@
 //    constant for the whole block: their product is formed once per block and
 //    every step multiplies only the touched rows into it (about 2x fewer
 //    products at density 0.2).
-//  * Products as in the dense real kernel.  The terms are summed exactly in a
-//    192-bit fixed-point integer per lane (fixacc.cuh) instead of a
-//    double-double: once the quiet rows made the products cheap, the
-//    double-double's ten FP64 instructions per step bound the kernel on the
-//    1/64-rate FP64 pipe.
+//  * Products, exact per-step double-double accumulation and the fixed-order
+//    reduction are those of the dense real kernel.
 #include <math.h>
 #include <stdint.h>
 #include <string.h>
@@ -31,7 +28,6 @@
 #include <mutex>
 
 #include "common.cuh"
-#include "fixacc.cuh"
 #include "kernels.h"
 #include "real.cuh"
 
@@ -55,7 +51,7 @@ struct SpArgs {
   int c;
   int one;
   uint64_t nchunks;
-  Fix192* part;
+  dd* part;
   unsigned int* counter;
   double* out;
   int32_t* status;
@@ -218,9 +214,7 @@ __global__ void __launch_bounds__(kSpBlock) ryser_sparse_kernel(SpArgs a) {
   const uint64_t nwarps = (uint64_t)(gridDim.x * kSpBlock) >> 5;
   const uint64_t ngroups = skip ? 0 : (a.nchunks + 31) / 32;
   const uint32_t nsteps = 1u << a.c;
-  Fix192 acc;
-  fix_zero(acc);
-  const int L0 = fix_l0(sh.bound_log2, n);
+  dd acc = {0.0, 0.0};
 
   for (uint64_t q = warp_id; q < ngroups; q += nwarps) {
     if (should_abort(a.abort_word, a.aborted)) break;
@@ -301,23 +295,29 @@ __global__ void __launch_bounds__(kSpBlock) ryser_sparse_kernel(SpArgs a) {
         }
         epos += prod_mul(pa, pb.m0, pb.m1);
         epos += prod_mul(pa, pq.m0, pq.m1);
-        // the term is M 2^(f - 1084) with f the biased binary64 exponent minus one
         const int f = F0 + (int)epos;
-        fix_add(acc, pa.m0, pa.m1, f - 1084 - L0, (neg ^ t ^ gpar) & 1u);
+        const uint32_t signbit = (neg ^ t ^ gpar) << 31;
+        double th, tl;
+        prod_to_dd(pa, (uint32_t)max(f, 0), signbit, th, tl);
+        dd_acc(acc, th, tl);
       }
     }
+    acc = dd_make(acc.hi, acc.lo);
   }
 
-  // reduction (exact integer sums): warps -> CTA -> last CTA
-  const Fix192 b = fix_block_sum<kSpWarps>(acc);
-  if (tid == 0) a.part[blockIdx.x] = b;
+  // reduction (fixed order): warps -> CTA -> last CTA
+  __shared__ dd s_w[kSpWarps];
+  dd v = dd_warp_sum(acc);
+  if (lane == 0) s_w[tid >> 5] = v;
+  __syncthreads();
+  if (tid == 0) {
+    dd b = {0.0, 0.0};
+    for (int w = 0; w < kSpWarps; ++w) b = dd_add(b, s_w[w]);
+    a.part[blockIdx.x] = b;
+  }
   if (!arrive_last(a.counter)) return;
   if (tid < 32) {
-    Fix192 r;
-    fix_zero(r);
-    for (unsigned int i = tid; i < gridDim.x; i += 32) fix_add_fix(r, a.part[i]);
-    r = fix_warp_sum(r);
-    const dd tot = fix_to_dd(r, L0);
+    dd tot = dd_sum_partials(a.part, gridDim.x);
     if (tid == 0) {
       int32_t st = PERM_OK;
       if (sh.bad) st = PERM_EINVAL;
@@ -379,12 +379,12 @@ extern "C" int perm_sparse(int n, const int32_t* cptrs, const int32_t* rids, con
   const uint64_t need = ((nchunks + 31) / 32 + kSpWarps - 1) / kSpWarps;
   const int grid = (int)(need < (uint64_t)grid_full ? (need > 0 ? need : 1) : grid_full);
   void* ws = nullptr;
-  const size_t bytes = sizeof(Fix192) * (size_t)grid + 16;
+  const size_t bytes = sizeof(dd) * (size_t)grid + 16;
   if (cudaMallocAsync(&ws, bytes, s) != cudaSuccess) {
     cudaGetLastError();
     return PERM_ENOMEM;
   }
-  unsigned int* counter = reinterpret_cast<unsigned int*>(static_cast<char*>(ws) + sizeof(Fix192) * (size_t)grid);
+  unsigned int* counter = reinterpret_cast<unsigned int*>(static_cast<char*>(ws) + sizeof(dd) * (size_t)grid);
   if (cudaMemsetAsync(counter, 0, 2 * sizeof(unsigned int), s) != cudaSuccess) {
     cudaFreeAsync(ws, s);
     return PERM_ECUDA;
@@ -399,7 +399,7 @@ extern "C" int perm_sparse(int n, const int32_t* cptrs, const int32_t* rids, con
   args.c = c;
   args.one = 1;
   args.nchunks = nchunks;
-  args.part = static_cast<Fix192*>(ws);
+  args.part = static_cast<dd*>(ws);
   args.counter = counter;
   args.out = out;
   args.status = status;

@@ -98,3 +98,28 @@ def test_malformed_ccs_is_rejected(pg):
     Z = ok.copy()
     Z[2] = 0.0
     assert pg.perm_sparse(*_ccs(Z)) == 0.0
+
+
+def test_signed_and_dense_inputs_keep_their_accuracy(pg, oracle):
+    """Signed values (terms far below the row-sum bound) and a dense matrix
+    given as CCS: the per-term rounding must stay relative to each term, so
+    the result meets the dense kernel's accuracy, and J_n (the cancellation
+    worst case of Sec. 5) comes out as n!."""
+    import math
+
+    import torch
+
+    g = syn.rng(4100)
+    for n, density in ((16, 0.3), (22, 0.25), (20, 1.0)):
+        mask = g.random((n, n)) < density
+        np.fill_diagonal(mask, True)
+        A = np.where(mask, 2.0 * g.random((n, n)) - 1.0, 0.0)
+        got = pg.perm_sparse(*_ccs(A))
+        want = oracle.perm_dp_f64(A)
+        scale = oracle.perm_dp_f64(np.abs(A))
+        assert abs(got - want) <= 1e-10 * scale
+        assert abs(got - want) <= 1e-9 * abs(want) + 1e-14 * scale
+        dense = pg.perm(torch.from_numpy(A).cuda())
+        assert abs(got - dense) <= 1e-12 * max(abs(want), 1e-300) + 1e-15 * scale
+    J = np.ones((22, 22))
+    assert pg.perm_sparse(*_ccs(J)) == pytest.approx(float(math.factorial(22)), rel=1e-13)
