@@ -82,9 +82,8 @@ __device__ __forceinline__ void row_abs(unsigned long long Y, uint32_t& a0, uint
 // sum hi + lo of two binary64 numbers with no rounding: hi is M rounded to 53
 // bits (the implicit bit placed on the exponent field f, the biased exponent
 // minus one, clamped at 0 by the caller), lo = M - round(M) in [-512, 511]
-// units of 2^(f+1-1023-62).  Both are assembled with integer operations; only
-// the small int -> binary64 conversion and the power-of-two scaling of lo use
-// the FP64 pipe.
+// units of 2^(f+1-1023-62).  Both are assembled with integer operations; no
+// FP64 instruction is used.
 __device__ __forceinline__ void prod_to_dd(const Prod& p, uint32_t f, uint32_t signbit, double& hi, double& lo) {
   uint32_t rlo, rhi;
   asm("add.cc.u32 %0, %2, 512;\n\t"
@@ -94,12 +93,17 @@ __device__ __forceinline__ void prod_to_dd(const Prod& p, uint32_t f, uint32_t s
   const uint32_t lo32 = __funnelshift_r(rlo, rhi, 10);
   const uint32_t hi32 = (rhi >> 10) + (f << 20) + signbit;
   hi = __hiloint2double((int)hi32, (int)lo32);
-  // remainder M - (R with its low 10 bits cleared), |r| <= 512, with the sign
+  // remainder r = M - (R with its low 10 bits cleared), |r| <= 512; the tail
+  // is (-1)^sign r 2^(f - 61 - 1023), assembled from integers as well: the
+  // top bit of |r| sets the exponent, its (at most nine) lower bits the
+  // fraction; tails below the normal range flush to zero
   const int32_t r = (int32_t)(p.m0 - (rlo & 0xFFFFFC00u));
-  const int32_t sr = signbit ? -r : r;
-  // 2^(f + 1 - 1023 - 62) as binary64: biased exponent f - 61 (0 flushes)
-  const int32_t fe = max((int32_t)f - 61, 0);
-  lo = (double)sr * __hiloint2double(fe << 20, 0);
+  const uint32_t nr = (uint32_t)(r >> 31);
+  const uint32_t mag = ((uint32_t)r ^ nr) - nr;
+  const int lz = __clz((int)(mag | 1u));
+  const int be = (int)f - 61 + 31 - lz;
+  const uint32_t hw = ((nr & 0x80000000u) ^ signbit) | ((uint32_t)be << 20) | (((mag << lz) << 1) >> 12);
+  lo = (mag == 0u || be <= 0) ? 0.0 : __hiloint2double((int)hw, 0);
 }
 
 // Shared-memory layout (dynamic): Dpm[(2j + s) * NP + i] for j < n-1,
