@@ -201,6 +201,22 @@ int perm_grad_batched(const void* A, int n, int count, int type, void* out, void
                       void* stream);
 
 /*
+ * perm_grad_batched_mixed - perm_grad of `count` matrices of mixed orders.
+ *   ns_host       host int[count], orders 0..32;
+ *   A_packed      device; matrix m (row-major) starts at element
+ *                 offsets_host[m] (host int64[count]);
+ *   G_packed      device; gradient m is written at the same element offset;
+ *   out           device, count elements (perm of each matrix);
+ *   status        optional device int32: the first failing order's code.
+ * The host groups the matrices by order; each group is gathered into a
+ * contiguous batch, swept by one perm_grad_batched launch and scattered
+ * back.  Allocates a workspace and waits for the stream before returning.
+ */
+int perm_grad_batched_mixed(int type, const int* ns_host, int count, const void* A_packed,
+                            const int64_t* offsets_host, void* out, void* G_packed, int32_t* status,
+                            void* stream);
+
+/*
  * Sparse preprocessing (Sec. 4; host-side graph work, leaves on the GPU).
  *
  * perm_decomp_create builds, from a HOST CCS matrix (same validation as

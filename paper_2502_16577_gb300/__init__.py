@@ -21,7 +21,7 @@ import numpy as np
 from . import _lib
 from ._lib import PERM_BIN, PERM_C128, PERM_EABORTED, PERM_F64, PermError, check, load
 
-__all__ = ["perm", "perm_async", "perm_range", "perm_range_async", "perm_combine", "perm_sparse", "perm_sparse_async", "perm_host", "pipe_peaks", "BatchPlan", "AbortWord", "perm_grad", "perm_grad_async", "perm_grad_batched", "perm_grad_batched_async", "permanent", "perm_type_of", "PermError",
+__all__ = ["perm", "perm_async", "perm_range", "perm_range_async", "perm_combine", "perm_sparse", "perm_sparse_async", "perm_host", "pipe_peaks", "BatchPlan", "AbortWord", "perm_grad", "perm_grad_async", "perm_grad_batched", "perm_grad_batched_async", "perm_grad_mixed", "permanent", "perm_type_of", "PermError",
            "PERM_F64", "PERM_C128", "PERM_BIN", "PERM_EABORTED", "load"]
 
 
@@ -256,6 +256,40 @@ def perm_grad_batched(A, stream=None):
     s.synchronize()
     check(int(status.item()), "perm_grad_batched")
     return out, G
+
+
+def perm_grad_mixed(mats, device=None, stream=None):
+    """Permanents and gradients of a list of square matrices of mixed orders
+    (all float64 or all complex128) through perm_grad_batched_mixed; returns
+    (numpy array of permanents, list of numpy gradients)."""
+    torch = _torch()
+    lib = load()
+    device = device or torch.device("cuda")
+    arrs = [np.asarray(m.detach().cpu().numpy() if hasattr(m, "detach") else m) for m in mats]
+    cplx = any(np.iscomplexobj(a) for a in arrs)
+    dt = np.complex128 if cplx else np.float64
+    ns = [int(a.shape[0]) for a in arrs]
+    offs, total = [], 0
+    for n in ns:
+        offs.append(total)
+        total += n * n
+    host = np.zeros(max(total, 1), dtype=dt)
+    for a, o in zip(arrs, offs):
+        host[o:o + a.size] = np.asarray(a, dtype=dt).reshape(-1)
+    A = torch.from_numpy(host).to(device)
+    G = torch.zeros_like(A)
+    out = torch.zeros(len(ns), dtype=A.dtype, device=device)
+    status = torch.full((1,), -1, dtype=torch.int32, device=device)
+    h, s = _stream_handle(stream)
+    karr = (ctypes.c_int * max(len(ns), 1))(*ns)
+    oarr = (ctypes.c_int64 * max(len(ns), 1))(*offs)
+    check(lib.perm_grad_batched_mixed(PERM_C128 if cplx else PERM_F64, karr, len(ns), ctypes.c_void_p(A.data_ptr()),
+                                      oarr, ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(G.data_ptr()),
+                                      ctypes.c_void_p(status.data_ptr()), h), "perm_grad_batched_mixed")
+    s.synchronize()
+    check(int(status.item()), "perm_grad_batched_mixed")
+    g = G.cpu().numpy()
+    return out.cpu().numpy(), [g[o:o + n * n].reshape(n, n) for o, n in zip(offs, ns)]
 
 
 def _autograd_function():

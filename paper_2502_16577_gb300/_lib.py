@@ -19,7 +19,7 @@ _lib = None
 
 SYMBOLS = ("perm", "perm_range", "perm_combine", "perm_sparse", "perm_host", "perm_pipe_peaks",
            "perm_batched_plan_create", "perm_batched", "perm_batched_autotune", "perm_batched_plan_info",
-           "perm_batched_plan_destroy", "perm_grad", "perm_grad_batched", "perm_decomp_create", "perm_decomp_info", "perm_decomp_leaf",
+           "perm_batched_plan_destroy", "perm_grad", "perm_grad_batched", "perm_grad_batched_mixed", "perm_decomp_create", "perm_decomp_info", "perm_decomp_leaf",
            "perm_decomp_filtered", "perm_decomp_eval", "perm_decomp_destroy", "perm_sparse_decomp",
            "perm_set_abort_word", "perm_abort_word_alloc", "perm_abort_word_free",
            "perm_status_string", "perm_abi_version")
@@ -77,6 +77,9 @@ def load(build_if_missing: bool = False):
     lib.perm_grad.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp]
     lib.perm_grad_batched.restype = ctypes.c_int
     lib.perm_grad_batched.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp]
+    lib.perm_grad_batched_mixed.restype = ctypes.c_int
+    lib.perm_grad_batched_mixed.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int, _vp,
+                                            ctypes.POINTER(ctypes.c_int64), _vp, _vp, _vp, _vp]
     _dp = ctypes.POINTER(ctypes.c_double)
     _ip = ctypes.POINTER(ctypes.c_int)
     lib.perm_decomp_create.restype = ctypes.c_int

@@ -38,6 +38,7 @@
 #include <string.h>
 
 #include <mutex>
+#include <vector>
 
 #include "common.cuh"
 #include "real.cuh"
@@ -585,6 +586,34 @@ __global__ void grad_empty_kernel(double* out, int count, int W, int32_t* status
   if (i == 0 && status) *status = PERM_OK;
 }
 
+// Mixed sizes: gather the matrices of one order into a contiguous batch and
+// scatter its results back (one CTA per matrix).
+__global__ void grad_gather_kernel(const double* __restrict__ src, const int64_t* __restrict__ offs, int nn_w,
+                                   double* __restrict__ dst) {
+  const int m = blockIdx.x;
+  const double* s = src + offs[m];
+  double* d = dst + (size_t)m * nn_w;
+  for (int i = threadIdx.x; i < nn_w; i += blockDim.x) d[i] = s[i];
+}
+
+__global__ void grad_scatter_kernel(const double* __restrict__ G, const double* __restrict__ out, const int64_t* offs,
+                                    const int64_t* out_idx, int nn_w, int W, double* __restrict__ Gdst,
+                                    double* __restrict__ outdst) {
+  const int m = blockIdx.x;
+  const double* s = G + (size_t)m * nn_w;
+  double* d = Gdst + offs[m];
+  for (int i = threadIdx.x; i < nn_w; i += blockDim.x) d[i] = s[i];
+  if (threadIdx.x < W) outdst[out_idx[m] * W + threadIdx.x] = out[(size_t)m * W + threadIdx.x];
+}
+
+// status of a mixed call: the first failing group's code, else PERM_OK
+__global__ void grad_status_merge_kernel(const int32_t* st, int groups, int32_t* status) {
+  int32_t r = PERM_OK;
+  for (int g = 0; g < groups; ++g)
+    if (r == PERM_OK && st[g] != PERM_OK) r = st[g];
+  if (status) *status = r;
+}
+
 // ------------------------------------------------------------------ host
 
 using KernelFn = void (*)(GradArgs);
@@ -770,4 +799,86 @@ extern "C" int perm_grad_batched(const void* A, int n, int count, int type, void
 
 extern "C" int perm_grad(const void* A, int n, int type, void* out, void* G, int32_t* status, void* stream) {
   return perm_grad_batched(A, n, 1, type, out, G, status, stream);
+}
+
+extern "C" int perm_grad_batched_mixed(int type, const int* ns_host, int count, const void* A_packed,
+                                       const int64_t* offsets_host, void* out, void* G_packed, int32_t* status,
+                                       void* stream) {
+  if (type != PERM_F64 && type != PERM_C128) return PERM_EINVAL;
+  if (count < 0 || (count > 0 && (!ns_host || !offsets_host || !out))) return PERM_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int W = type == PERM_C128 ? 2 : 1;
+  if (count == 0)
+    return status ? (cudaMemsetAsync(status, 0, sizeof(int32_t), s) == cudaSuccess ? PERM_OK : PERM_ECUDA)
+                  : PERM_OK;
+  // group the matrices by order
+  std::vector<std::vector<int>> groups(33);
+  for (int m = 0; m < count; ++m) {
+    const int n = ns_host[m];
+    if (n < 0 || n > 32) return PERM_ERANGE;
+    if (offsets_host[m] < 0) return PERM_EINVAL;
+    if (n > 0 && (!A_packed || !G_packed)) return PERM_EINVAL;
+    groups[n].push_back(m);
+  }
+  int ngroups = 0;
+  size_t tmp_doubles = 0, idx_words = 0;
+  for (int n = 0; n <= 32; ++n)
+    if (!groups[n].empty()) {
+      ++ngroups;
+      tmp_doubles += groups[n].size() * ((size_t)n * n * W * 2 + W);
+      idx_words += 2 * groups[n].size();
+    }
+  void* ws = nullptr;
+  const size_t bytes = sizeof(double) * tmp_doubles + sizeof(int64_t) * idx_words + sizeof(int32_t) * 40 + 64;
+  if (cudaMalloc(&ws, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return PERM_ENOMEM;
+  }
+  double* tmp = static_cast<double*>(ws);
+  int64_t* idx = reinterpret_cast<int64_t*>(tmp + tmp_doubles);
+  int32_t* gst = reinterpret_cast<int32_t*>(idx + idx_words);
+  std::vector<int64_t> hidx(idx_words);
+  int rc = PERM_OK, g = 0;
+  size_t toff = 0, ioff = 0;
+  for (int n = 0; n <= 32 && rc == PERM_OK; ++n) {
+    const std::vector<int>& ms = groups[n];
+    if (ms.empty()) continue;
+    const int cnt = (int)ms.size();
+    const int nn_w = n * n * W;
+    double* Ag = tmp + toff;
+    double* Gg = Ag + (size_t)cnt * nn_w;
+    double* og = Gg + (size_t)cnt * nn_w;
+    toff += (size_t)cnt * ((size_t)nn_w * 2 + W);
+    int64_t* offs = idx + ioff;
+    int64_t* oidx = offs + cnt;
+    for (int k = 0; k < cnt; ++k) {
+      hidx[ioff + k] = offsets_host[ms[k]] * W;
+      hidx[ioff + cnt + k] = ms[k];
+    }
+    // pageable source: the copy has completed when cudaMemcpyAsync returns
+    if (cudaMemcpyAsync(offs, hidx.data() + ioff, sizeof(int64_t) * 2 * cnt, cudaMemcpyHostToDevice, s) !=
+        cudaSuccess)
+      rc = PERM_ECUDA;
+    ioff += 2 * (size_t)cnt;
+    if (rc == PERM_OK && n > 0) {
+      grad_gather_kernel<<<cnt, 128, 0, s>>>(static_cast<const double*>(A_packed), offs, nn_w, Ag);
+      if (cudaGetLastError() != cudaSuccess) rc = PERM_ECUDA;
+    }
+    if (rc == PERM_OK) rc = perm_grad_batched(Ag, n, cnt, type, og, Gg, gst + g, stream);
+    if (rc == PERM_OK) {
+      grad_scatter_kernel<<<cnt, 128, 0, s>>>(Gg, og, offs, oidx, nn_w, W, static_cast<double*>(G_packed),
+                                              static_cast<double*>(out));
+      if (cudaGetLastError() != cudaSuccess) rc = PERM_ECUDA;
+    }
+    ++g;
+  }
+  if (rc == PERM_OK) {
+    grad_status_merge_kernel<<<1, 1, 0, s>>>(gst, ngroups, status);
+    if (cudaGetLastError() != cudaSuccess) rc = PERM_ECUDA;
+  }
+  // the workspace is released after the stream's work on it
+  if (cudaStreamSynchronize(s) != cudaSuccess && rc == PERM_OK) rc = PERM_ECUDA;
+  if (cudaFree(ws) != cudaSuccess && rc == PERM_OK) rc = PERM_ECUDA;
+  if (rc != PERM_OK) cudaGetLastError();
+  return rc;
 }

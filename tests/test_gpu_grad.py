@@ -261,3 +261,27 @@ def test_config_complex_batch_1024_k16(pg, oracle):
     for p in (0, 511, 1023):
         assert abs(out[p] - oracle.perm_c128(Ms[p])) <= 1e-12
         _check_minors(G[p], Ms[p], oracle, cplx=True)
+
+
+def test_mixed_orders(pg, oracle):
+    """Matrices of mixed orders (0 .. 20, real and complex) in one call: each
+    gradient equals the single-matrix sweep, the permanents the oracle."""
+    g = syn.rng(12500)
+    ks = [3, 7, 0, 12, 7, 1, 20, 3, 16, 9, 12]
+    mats = [2.0 * g.random((k, k)) - 1.0 for k in ks]
+    perms, grads = pg.perm_grad_mixed(mats)
+    for M, p, G in zip(mats, perms, grads):
+        k = M.shape[0]
+        if k == 0:
+            assert p == 1.0
+            continue
+        scale = oracle.perm_dp_f64(np.abs(M))
+        assert abs(p - oracle.perm_dp_f64(M)) <= 1e-12 * scale
+        _, Gs = pg.perm_grad(_dev(M))
+        assert np.max(np.abs(G - Gs.cpu().numpy())) <= 1e-12 * scale
+    cm = syn.boson_submatrices(30, 12600, 5, 17, 64)
+    perms, grads = pg.perm_grad_mixed(cm)
+    for M, p, G in zip(cm, perms, grads):
+        assert abs(p - oracle.perm_c128(M)) <= 1e-12
+        _, Gs = pg.perm_grad(_dev(M))
+        assert np.max(np.abs(G - Gs.cpu().numpy())) <= 1e-13
