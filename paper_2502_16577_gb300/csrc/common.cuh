@@ -1,9 +1,9 @@
 // Shared device helpers of the permanent kernels (GB300, sm_103a).
 //
 // Nothing here is specific to one element type: double-double accumulation
-// (Knuth's TwoSum, the "quad as two doubles" outer sum of Sec. 5), warp and
-// block reductions in a fixed order, the launch argument block, and the
-// integer helpers of the fixed-point product.
+// (the "quad as two doubles" outer sum of Sec. 5, with exact Fast2Sum / TwoSum
+// steps), warp and block reductions in a fixed order, the launch argument
+// block, cancellation, and the integer helpers of the fixed-point product.
 #pragma once
 
 #include <cuda_runtime.h>

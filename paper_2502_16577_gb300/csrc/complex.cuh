@@ -10,9 +10,8 @@
 // handling:  (p1 2^31 + p0)(y1 2^31 + y0) = p1 y1 2^62 + (p1 y0 + p0 y1) 2^31 + ...
 // After each complex multiply the pair is renormalised so that the larger part
 // has its top bit at 2^60.  Each part of a term is split exactly into a
-// binary64 head and tail (the conversions run on the otherwise idle FP64
-// pipe) and added to double-double lane partials with an exact TwoSum
-// (Sec. 5).
+// binary64 head and tail and added to double-double lane partials with an
+// exact two-sum (dd_acc, Sec. 5).
 #pragma once
 
 #include "common.cuh"

@@ -12,10 +12,10 @@
 //    power-of-two count: three 32x32->64 multiply-adds and one renormalising
 //    shift per factor (relative error below 2^-60 per factor).
 //  * Each step's signed term is split without rounding into a binary64 head
-//    (assembled from the integer mantissa and exponent) and a small tail, and
-//    added to a per-lane double-double with an exact TwoSum (Sec. 5's "quad"
-//    outer sum, applied to every term): the only roundings left are the
-//    62-bit products and the double-double itself.
+//    and a small tail, both assembled from the integer mantissa and exponent,
+//    and added to a per-lane double-double with an exact Fast2Sum (Sec. 5's
+//    "quad" outer sum, applied to every term): the only roundings left are
+//    the 62-bit products and the double-double itself.
 //  * The matrix is staged in shared memory as signed column increments
 //    (+D_j and -D_j, j < n-1), column-contiguous; all lanes of a warp flip the
 //    same column at the same step (aligned chunks, Sec. 3.1.1), so every
