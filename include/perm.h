@@ -20,7 +20,9 @@
  *     column n is column n-1 here.
  *   - "device" pointers are CUDA device (or managed) memory on the current
  *     device; "host" pointers are ordinary host memory.  The caller owns every
- *     buffer; the library never frees or keeps a caller pointer.
+ *     buffer and the library never frees one.  Only a batched plan (its bound
+ *     input / output buffers) and the registered abort word keep a caller
+ *     pointer beyond the call, as documented at those entry points.
  *   - stream is a cudaStream_t passed as void* (NULL = legacy default stream).
  *     Device-pointer calls are stream-ordered and return without waiting for
  *     the GPU; they take their scratch memory with cudaMallocAsync on that
@@ -42,7 +44,7 @@
 extern "C" {
 #endif
 
-#define PERM_ABI_VERSION 1
+#define PERM_ABI_VERSION 2
 #define PERM_NMAX 63
 
 typedef enum {

@@ -45,10 +45,24 @@ def test_exports_every_declared_symbol(lib):
 
 
 def test_abi_version_and_status_strings(lib):
-    assert lib.perm_abi_version() == 1
-    for code in range(6):
-        assert lib.perm_status_string(code)
+    import re
+
+    header = open(os.path.join(ROOT, "include", "perm.h")).read()
+    assert lib.perm_abi_version() == int(re.search(r"#define PERM_ABI_VERSION (\d+)", header).group(1))
+    for code in range(7):
+        assert b"unknown" not in lib.perm_status_string(code)
     assert b"unknown" in lib.perm_status_string(99)
+
+
+def test_new_entry_points_check_arguments_on_the_host(lib):
+    vp = ctypes.c_void_p
+    dummy = vp(16)
+    # gradient: type, order and count are checked before any CUDA call
+    assert lib.perm_grad(dummy, 4, 2, dummy, dummy, vp(0), vp(0)) == 1       # 0/1 type
+    assert lib.perm_grad(dummy, 33, 0, dummy, dummy, vp(0), vp(0)) == 2      # n > 32
+    assert lib.perm_grad_batched(dummy, 4, -1, 0, dummy, dummy, vp(0), vp(0)) == 1
+    # cancellation word: unregistering needs no device
+    assert lib.perm_set_abort_word(None) == 0
 
 
 def test_host_argument_checks_need_no_gpu(lib):

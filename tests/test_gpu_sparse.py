@@ -73,6 +73,17 @@ def test_tridiagonal_n44_full_size(pg, oracle):
     assert got == float(oracle.fibonacci(n + 1))
 
 
+def test_config_sparse_n44_block_diagonal_full_size(pg, oracle):
+    """The sparse n = 44 configuration at full size (2^43 Gray steps through
+    the sparse kernel): two 22 x 22 density-0.2 blocks, rows and columns
+    shuffled, so the answer is the product of the two block permanents."""
+    B1, B2 = syn.sparse_real(22, 4401, 0.2), syn.sparse_real(22, 4402, 0.2)
+    M = syn.shuffle_rows_cols(syn.block_diagonal([B1, B2]), 4403)
+    want = oracle.perm_f64(B1) * oracle.perm_f64(B2)
+    got = pg.perm_sparse(*_ccs(M))
+    assert got == pytest.approx(want, rel=1e-10)
+
+
 def test_block_diagonal_n32(pg, oracle):
     B1, B2 = syn.sparse_real(16, 1, 0.3), syn.sparse_real(16, 2, 0.3)
     M = syn.shuffle_rows_cols(syn.block_diagonal([B1, B2]), 3)
