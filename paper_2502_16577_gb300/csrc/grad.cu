@@ -14,7 +14,7 @@
 //
 // GB300 layout:
 //  * A sub-group of 8 lanes walks one aligned chunk; lane l owns rows
-//    R l .. R l + R - 1 (R = 1, 2 or 4, so 8 R >= n), four sub-groups per warp
+//    R l .. R l + R - 1 (R = 1..4, the least with 8 R >= n), four sub-groups per warp
 //    on four neighbouring chunks.  Rows are staged as in the forward kernels:
 //    64-bit fixed point per row with a power-of-two row scale, one exact
 //    integer add per row and step.
@@ -400,6 +400,12 @@ __global__ void __launch_bounds__(kGThreads, (CPLX && R == 4) ? 2 : 4) ryser_gra
         ex[0] = lf[1];
         ex[1] = lf[0];
         grp = mul(lf[0], lf[1]);
+      } else if constexpr (R == 3) {
+        const E p01 = mul(lf[0], lf[1]);
+        ex[0] = mul(lf[1], lf[2]);
+        ex[1] = mul(lf[0], lf[2]);
+        ex[2] = p01;
+        grp = mul(p01, lf[2]);
       } else {
         const E p01 = mul(lf[0], lf[1]), p23 = mul(lf[2], lf[3]);
         ex[0] = mul(lf[1], p23);
@@ -619,8 +625,15 @@ __global__ void grad_status_merge_kernel(const int32_t* st, int groups, int32_t*
 using KernelFn = void (*)(GradArgs);
 
 KernelFn grad_kernel(bool cplx, int R) {
-  if (cplx) return R == 1 ? ryser_grad_kernel<true, 1> : R == 2 ? ryser_grad_kernel<true, 2> : ryser_grad_kernel<true, 4>;
-  return R == 1 ? ryser_grad_kernel<false, 1> : R == 2 ? ryser_grad_kernel<false, 2> : ryser_grad_kernel<false, 4>;
+  if (cplx)
+    return R == 1   ? ryser_grad_kernel<true, 1>
+           : R == 2 ? ryser_grad_kernel<true, 2>
+           : R == 3 ? ryser_grad_kernel<true, 3>
+                    : ryser_grad_kernel<true, 4>;
+  return R == 1   ? ryser_grad_kernel<false, 1>
+         : R == 2 ? ryser_grad_kernel<false, 2>
+         : R == 3 ? ryser_grad_kernel<false, 3>
+                  : ryser_grad_kernel<false, 4>;
 }
 
 size_t grad_smem(bool cplx, int n, int R, int cq) {
@@ -653,7 +666,7 @@ int device_prepare(int dev) {
     // the dynamic limit plus the kernel's static shared memory must stay
     // within the opt-in maximum
     for (int c = 0; c < 2; ++c)
-      for (int R = 1; R <= 4; R *= 2) {
+      for (int R = 1; R <= 4; ++R) {
         const void* fn = reinterpret_cast<const void*>(grad_kernel(c != 0, R));
         cudaFuncAttributes fa;
         if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess ||
@@ -694,7 +707,7 @@ extern "C" int perm_grad_batched(const void* A, int n, int count, int type, void
   if (cudaGetDevice(&dev) != cudaSuccess) return PERM_ECUDA;
   const int sms = device_prepare(dev);
   if (sms <= 0) return PERM_ECUDA;
-  const int R = n <= 8 ? 1 : n <= 16 ? 2 : 4;
+  const int R = n <= 8 ? 1 : n <= 16 ? 2 : n <= 24 ? 3 : 4;
   const int NR = kGL * R;
   KernelFn fn = grad_kernel(cplx, R);
 
