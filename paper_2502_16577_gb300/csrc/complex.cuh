@@ -33,28 +33,62 @@ __device__ __forceinline__ void cprod_init(CProd& p) {
 
 // p <- p * y for y = (yr, yi) signed with |yr|, |yi| < 2^61.  Returns the
 // renormalising shift s (the product was multiplied by 2^(s-62)).
+//   middle partial products (scale 2^31):
+//     tr = r1 yr0 + r0 yr1 - i1 yi0 - i0 yi1,  ti = r1 yi0 + r0 yi1 + i1 yr0 + i0 yr1
+//   high partial products (scale 2^62) plus the carried middle part:
+//     vr = r1 yr1 - i1 yi1 + (tr >> 31),  vi = r1 yi1 + i1 yr1 + (ti >> 31)
+//   then the larger part's top bit is shifted to 2^60 and both parts are
+//   split back into limbs.  Written as PTX signed wide multiply-adds with the
+//   negated limbs formed once: a quarter fewer instructions than the same
+//   arithmetic in C++ (measured), with bitwise-identical results.
 __device__ __forceinline__ int cprod_mul(CProd& p, long long yr, long long yi) {
-  const int32_t yr1 = (int32_t)(yr >> 31), yi1 = (int32_t)(yi >> 31);
-  const int32_t yr0 = (int32_t)((uint32_t)yr & 0x7FFFFFFFu), yi0 = (int32_t)((uint32_t)yi & 0x7FFFFFFFu);
-  const int32_t nr0 = (int32_t)p.r0, ni0 = (int32_t)p.i0;
-  // middle partial products (scale 2^31), |t| < 2^63
-  long long tr = (long long)p.r1 * yr0 + (long long)nr0 * yr1 - (long long)p.i1 * yi0 - (long long)ni0 * yi1;
-  long long ti = (long long)p.r1 * yi0 + (long long)nr0 * yi1 + (long long)p.i1 * yr0 + (long long)ni0 * yr1;
-  // high partial products (scale 2^62) plus the carried middle part
-  long long vr = (long long)p.r1 * yr1 - (long long)p.i1 * yi1 + (tr >> 31);
-  long long vi = (long long)p.r1 * yi1 + (long long)p.i1 * yr1 + (ti >> 31);
-  // top set bit of max(|vr|, |vi|) (ones' complement magnitude of the high words)
-  const uint32_t hr = (uint32_t)((unsigned long long)vr >> 32), hi = (uint32_t)((unsigned long long)vi >> 32);
-  const uint32_t w = (hr ^ (uint32_t)((int32_t)hr >> 31)) | (hi ^ (uint32_t)((int32_t)hi >> 31));
-  int pos;
-  asm("bfind.u32 %0, %1;" : "=r"(pos) : "r"(w));  // -1 when w == 0
-  // shift so that the top bit lands at 2^60 (bit 28 of the high word)
-  const int s = 28 - pos;  // in [0, 29]; 29 when both parts are tiny
-  const long long nr = vr << s, ni = vi << s;
-  p.r1 = (int32_t)(nr >> 31);
-  p.r0 = (uint32_t)nr & 0x7FFFFFFFu;
-  p.i1 = (int32_t)(ni >> 31);
-  p.i0 = (uint32_t)ni & 0x7FFFFFFFu;
+  int s;
+  asm("{\n\t"
+      ".reg .s64 tr, ti, vr, vi;\n\t"
+      ".reg .s32 yr1, yr0, yi1, yi0, ni1, ni0, vrh, vih, m1, m2, a1, a2, w, pos;\n\t"
+      ".reg .u32 ul, uh;\n\t"
+      "mov.b64 {ul, uh}, %5;\n\t"
+      "shf.l.wrap.b32 yr1, ul, uh, 1;\n\t"
+      "and.b32 yr0, ul, 0x7FFFFFFF;\n\t"
+      "mov.b64 {ul, uh}, %6;\n\t"
+      "shf.l.wrap.b32 yi1, ul, uh, 1;\n\t"
+      "and.b32 yi0, ul, 0x7FFFFFFF;\n\t"
+      "neg.s32 ni1, %3;\n\t"
+      "neg.s32 ni0, %4;\n\t"
+      "mul.wide.s32 tr, %1, yr0;\n\t"
+      "mad.wide.s32 tr, %2, yr1, tr;\n\t"
+      "mad.wide.s32 tr, ni1, yi0, tr;\n\t"
+      "mad.wide.s32 tr, ni0, yi1, tr;\n\t"
+      "mul.wide.s32 ti, %1, yi0;\n\t"
+      "mad.wide.s32 ti, %2, yi1, ti;\n\t"
+      "mad.wide.s32 ti, %3, yr0, ti;\n\t"
+      "mad.wide.s32 ti, %4, yr1, ti;\n\t"
+      "shr.s64 tr, tr, 31;\n\t"
+      "shr.s64 ti, ti, 31;\n\t"
+      "mad.wide.s32 vr, %1, yr1, tr;\n\t"
+      "mad.wide.s32 vr, ni1, yi1, vr;\n\t"
+      "mad.wide.s32 vi, %1, yi1, ti;\n\t"
+      "mad.wide.s32 vi, %3, yr1, vi;\n\t"
+      "mov.b64 {ul, vrh}, vr;\n\t"
+      "mov.b64 {ul, vih}, vi;\n\t"
+      "shr.s32 m1, vrh, 31;\n\t"
+      "xor.b32 a1, vrh, m1;\n\t"
+      "shr.s32 m2, vih, 31;\n\t"
+      "xor.b32 a2, vih, m2;\n\t"
+      "or.b32 w, a1, a2;\n\t"
+      "bfind.u32 pos, w;\n\t"  // -1 when both parts are tiny: shift 29
+      "sub.s32 %0, 28, pos;\n\t"
+      "shl.b64 vr, vr, %0;\n\t"
+      "shl.b64 vi, vi, %0;\n\t"
+      "mov.b64 {ul, uh}, vr;\n\t"
+      "shf.l.wrap.b32 %1, ul, uh, 1;\n\t"
+      "and.b32 %2, ul, 0x7FFFFFFF;\n\t"
+      "mov.b64 {ul, uh}, vi;\n\t"
+      "shf.l.wrap.b32 %3, ul, uh, 1;\n\t"
+      "and.b32 %4, ul, 0x7FFFFFFF;\n\t"
+      "}"
+      : "=r"(s), "+r"(p.r1), "+r"(p.r0), "+r"(p.i1), "+r"(p.i0)
+      : "l"(yr), "l"(yi));
   return s;
 }
 

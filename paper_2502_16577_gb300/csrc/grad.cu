@@ -122,21 +122,51 @@ struct CE {
 };
 
 __device__ __forceinline__ CE mul(CE a, CE b) {
-  const int32_t ar0 = (int32_t)a.r0, ai0 = (int32_t)a.i0, br0 = (int32_t)b.r0, bi0 = (int32_t)b.i0;
-  // middle partial products (scale 2^31); the low x low ones are dropped
-  const long long tr = (long long)a.r1 * br0 + (long long)ar0 * b.r1 - (long long)a.i1 * bi0 - (long long)ai0 * b.i1;
-  const long long ti = (long long)a.r1 * bi0 + (long long)ar0 * b.i1 + (long long)a.i1 * br0 + (long long)ai0 * b.r1;
-  // high partial products (scale 2^62)
-  const long long vr = (long long)a.r1 * b.r1 - (long long)a.i1 * b.i1 + (tr >> 31);
-  const long long vi = (long long)a.r1 * b.i1 + (long long)a.i1 * b.r1 + (ti >> 31);
-  const uint32_t hr = (uint32_t)((unsigned long long)vr >> 32), hi = (uint32_t)((unsigned long long)vi >> 32);
-  const uint32_t w = (hr ^ (uint32_t)((int32_t)hr >> 31)) | (hi ^ (uint32_t)((int32_t)hi >> 31));
-  int pos;
-  asm("bfind.u32 %0, %1;" : "=r"(pos) : "r"(w));  // -1 when both parts are tiny
-  const int s = 28 - pos;                           // top bit to 2^60
-  const long long nr = vr << s, ni = vi << s;
-  return CE{(int32_t)(nr >> 31), (int32_t)(ni >> 31), (uint32_t)nr & 0x7FFFFFFFu, (uint32_t)ni & 0x7FFFFFFFu,
-            a.e + b.e + 62 - s};
+  // the limb arithmetic of cprod_mul (complex.cuh), both operands already in
+  // limbs: middle partial products (scale 2^31), high ones (scale 2^62),
+  // renormalisation of the larger part to 2^60, limb split
+  int s;
+  asm("{\n\t"
+      ".reg .s64 tr, ti, vr, vi;\n\t"
+      ".reg .s32 ni1, ni0, vrh, vih, m1, m2, a1, a2, w, pos;\n\t"
+      ".reg .u32 ul, uh;\n\t"
+      "neg.s32 ni1, %3;\n\t"
+      "neg.s32 ni0, %4;\n\t"
+      "mul.wide.s32 tr, %1, %6;\n\t"
+      "mad.wide.s32 tr, %2, %5, tr;\n\t"
+      "mad.wide.s32 tr, ni1, %8, tr;\n\t"
+      "mad.wide.s32 tr, ni0, %7, tr;\n\t"
+      "mul.wide.s32 ti, %1, %8;\n\t"
+      "mad.wide.s32 ti, %2, %7, ti;\n\t"
+      "mad.wide.s32 ti, %3, %6, ti;\n\t"
+      "mad.wide.s32 ti, %4, %5, ti;\n\t"
+      "shr.s64 tr, tr, 31;\n\t"
+      "shr.s64 ti, ti, 31;\n\t"
+      "mad.wide.s32 vr, %1, %5, tr;\n\t"
+      "mad.wide.s32 vr, ni1, %7, vr;\n\t"
+      "mad.wide.s32 vi, %1, %7, ti;\n\t"
+      "mad.wide.s32 vi, %3, %5, vi;\n\t"
+      "mov.b64 {ul, vrh}, vr;\n\t"
+      "mov.b64 {ul, vih}, vi;\n\t"
+      "shr.s32 m1, vrh, 31;\n\t"
+      "xor.b32 a1, vrh, m1;\n\t"
+      "shr.s32 m2, vih, 31;\n\t"
+      "xor.b32 a2, vih, m2;\n\t"
+      "or.b32 w, a1, a2;\n\t"
+      "bfind.u32 pos, w;\n\t"
+      "sub.s32 %0, 28, pos;\n\t"
+      "shl.b64 vr, vr, %0;\n\t"
+      "shl.b64 vi, vi, %0;\n\t"
+      "mov.b64 {ul, uh}, vr;\n\t"
+      "shf.l.wrap.b32 %1, ul, uh, 1;\n\t"
+      "and.b32 %2, ul, 0x7FFFFFFF;\n\t"
+      "mov.b64 {ul, uh}, vi;\n\t"
+      "shf.l.wrap.b32 %3, ul, uh, 1;\n\t"
+      "and.b32 %4, ul, 0x7FFFFFFF;\n\t"
+      "}"
+      : "=r"(s), "+r"(a.r1), "+r"(a.r0), "+r"(a.i1), "+r"(a.i0)
+      : "r"(b.r1), "r"(b.r0), "r"(b.i1), "r"(b.i0));
+  return CE{a.r1, a.i1, a.r0, a.i0, a.e + b.e + 62 - s};
 }
 
 __device__ __forceinline__ CE shfl_xor(CE x, int d) {
