@@ -109,3 +109,39 @@ def test_config_binary_36_sampled_and_properties(pg, oracle):
     B1, B2 = syn.bernoulli01(18, 1, 0.5), syn.bernoulli01(18, 2, 0.5)
     M = syn.shuffle_rows_cols(syn.block_diagonal([B1, B2]), 3)
     assert pg.perm(_dev(M)) == oracle.perm_dp_bin(B1) * oracle.perm_dp_bin(B2)
+
+
+
+def _abs_glynn_sum(B):
+    """S = sum over all sign vectors d in {+-1}^m of prod_i |(1/2) sum_j d_j B_ij|
+    (the absolute terms of Eq. 2 for one diagonal block, numpy, exact in fp64
+    for 18 x 18 0/1 blocks: every factor is a multiple of 1/2 below 10)."""
+    m = B.shape[1]
+    bits = (np.arange(1 << m)[:, None] >> np.arange(m)) & 1
+    D = 1.0 - 2.0 * bits
+    return float(np.prod(np.abs(D @ B.T.astype(np.float64)) / 2.0, axis=1).sum())
+
+
+def test_full_size_fp64_kernel_on_01_input_vs_exact_integer(pg, oracle):
+    """The FP64 kernel's true error at full size (n = 36, 2^35 steps) on a 0/1
+    matrix with a known exact permanent: two 18 x 18 Bernoulli(0.5) blocks,
+    rows and columns shuffled, perm = the product of the block permanents
+    (oracle subset DP, exact integers).  The 0/1 kernel must match exactly.
+    The FP64 bound is derived, not tuned: rows are exact for 0/1 input, each
+    term's 62-bit product is off by < (n+1) 2^-61 relative, so
+    |err| <= 2 (n+1) 2^-61 sum_g |term_g|, and for a block-diagonal matrix the
+    half-sum of |terms| factors as S(B1) S(B2) / 2 (Sec. 5)."""
+    import torch
+
+    B1, B2 = syn.bernoulli01(18, 3601), syn.bernoulli01(18, 3602)
+    M = syn.shuffle_rows_cols(syn.block_diagonal([B1, B2]), 3603)
+    exact = oracle.perm_dp_bin(B1) * oracle.perm_dp_bin(B2)
+    assert exact > 0
+    assert pg.perm(torch.from_numpy(M.astype(np.uint8)).cuda()) == exact
+    got = pg.perm(torch.from_numpy(M.astype(np.float64)).cuda())
+    n = M.shape[0]
+    abs_terms = _abs_glynn_sum(B1) * _abs_glynn_sum(B2) / 2.0
+    bound = 2.0 * (n + 1) * 2.0**-61 * abs_terms + 2.0**-52 * exact
+    err = abs(got - exact)
+    print(f"n=36 0/1: exact {exact}, fp64 rel err {err / exact:.3e}, bound {bound / exact:.3e}")
+    assert err <= bound
