@@ -450,7 +450,8 @@ def measure_grad(pg, dev, stream, reps: int = 3):
 
 def run_case(args):
     """One kernel on one input, for profiling and sweeps: KIND:N with KIND in
-    real (uniform [-1, 1)), bin (Bernoulli 0.5), cplx (Haar unitary), sparse
+    real (uniform [-1, 1)), realx (the same with extended-precision products),
+    bin (Bernoulli 0.5), cplx (Haar unitary), sparse
     (density 0.2, CCS), grad (real, fused gradient), bgrad (1024 complex N x N
     boson submatrices, batched gradient).  Prints one JSON line."""
     import torch
@@ -465,12 +466,12 @@ def run_case(args):
     st = torch.zeros(1, dtype=torch.int32, device=dev)
     seed = syn.SEED_BASE + 100 + n
     steps = 1 << (n - 1)
-    if kind in ("real", "bin", "cplx"):
-        A = {"real": lambda: syn.signed_real(n, seed), "bin": lambda: syn.bernoulli01(n, seed),
-             "cplx": lambda: syn.haar_unitary(n, seed)}[kind]()
+    if kind in ("real", "realx", "bin", "cplx"):
+        A = {"real": lambda: syn.signed_real(n, seed), "realx": lambda: syn.signed_real(n, seed),
+             "bin": lambda: syn.bernoulli01(n, seed), "cplx": lambda: syn.haar_unitary(n, seed)}[kind]()
         A = torch.from_numpy(A).to(dev)
         out = torch.zeros(4, dtype=torch.int64 if kind == "bin" else torch.float64, device=dev)
-        fn = lambda: pg.perm_async(A, out, st, stream)
+        fn = lambda: pg.perm_async(A, out, st, stream, extended=kind == "realx")
     elif kind == "sparse":
         cp, ri, cv = syn.to_ccs(syn.sparse_real(n, seed, 0.2))
         cp, ri, cv = (torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in (cp, ri, cv))

@@ -44,13 +44,15 @@
 extern "C" {
 #endif
 
-#define PERM_ABI_VERSION 2
+#define PERM_ABI_VERSION 3
 #define PERM_NMAX 63
 
 typedef enum {
   PERM_F64 = 0,  /* real binary64 entries                                   */
   PERM_C128 = 1, /* complex entries, (re, im) binary64 pairs                 */
-  PERM_BIN = 2   /* 0/1 entries as uint8; the result is exact               */
+  PERM_BIN = 2,  /* 0/1 entries as uint8; the result is exact               */
+  PERM_F64X = 3  /* real binary64 entries, extended-precision products and a
+                    double-double result (Sec. 5's quad inner product)       */
 } perm_type_t;
 
 typedef enum {
@@ -67,14 +69,15 @@ typedef enum {
 /*
  * perm - permanent of one dense n x n matrix (Eq. 1 by Alg. 1 + Alg. 3).
  *
- *   A      device; PERM_F64: double[n*n]; PERM_C128: double[2*n*n] as (re, im)
- *          pairs; PERM_BIN: uint8_t[n*n] holding only 0 and 1.
+ *   A      device; PERM_F64, PERM_F64X: double[n*n]; PERM_C128: double[2*n*n]
+ *          as (re, im) pairs; PERM_BIN: uint8_t[n*n] holding only 0 and 1.
  *   out    device; PERM_F64: double[1]; PERM_C128: double[2] = (re, im);
  *          PERM_BIN: uint64_t[2] = the permanent as a little-endian unsigned
- *          128-bit integer.
+ *          128-bit integer; PERM_F64X: double[2] = (hi, lo), the permanent as
+ *          the unevaluated sum hi + lo with |lo| <= ulp(hi) / 2.
  *   status device int32_t[1] or NULL; receives PERM_OK, PERM_EINVAL (a
  *          non-finite entry, or a BIN entry other than 0/1: out is then NaN /
- *          zero), PERM_ERANGE (PERM_F64/C128 only: the largest possible term
+ *          zero), PERM_ERANGE (PERM_F64/F64X/C128: the largest possible term
  *          exceeds the binary64 range; out is then NaN) or PERM_EOVERFLOW
  *          (PERM_BIN only: perm(A) may be >= 2^128; out is then zero).
  *
@@ -82,6 +85,12 @@ typedef enum {
  * power-of-two scale per row (error at most 2^-60 of the row's absolute sum)
  * and the row vector x is kept exactly; products carry 62-bit mantissas and
  * the signed sum is accumulated in binary64 with a double-double carry.
+ * PERM_F64X uses the same fixed-point rows (column n-1 rounded to nearest,
+ * so a row is exact when every a_ij 2^(60-k) is an integer, k the binary
+ * exponent of the row's absolute sum) with 128-bit product mantissas
+ * (2^-124 per factor), splits every term into a double-double without
+ * losing more than 2^-105 of it, and renormalises the double-double after
+ * every step; it costs about 3x PERM_F64.
  * Binary matrices run in exact wrap-around integer arithmetic (192 bits).
  * Results are bitwise reproducible for a given n, type and GPU model.
  */
@@ -94,7 +103,7 @@ int perm(const void* A, int n, int type, void* out, int32_t* status, void* strea
  * the only exchange is the final sum).
  *
  *   partial device;
- *     PERM_F64:  double[2]   = (hi, lo) of  sum_g (-1)^g prod_i x_i(g);
+ *     PERM_F64, PERM_F64X: double[2] = (hi, lo) of  sum_g (-1)^g prod_i x_i(g);
  *     PERM_C128: double[4]   = (re hi, re lo, im hi, im lo) of the same sum;
  *     PERM_BIN:  uint64_t[3] = sum_g (-1)^g prod_i x'_i(g) modulo 2^192,
  *                little-endian, with the doubled integer rows x' = 2x.
@@ -109,7 +118,8 @@ int perm_range(const void* A, int n, int type, uint64_t g_begin, uint64_t g_end,
 /*
  * perm_combine - host-side reduction of perm_range partials that together
  * cover [0, 2^(n-1)) exactly once, in the order given, into the perm() output
- * format: multiply by 2 (-1)^(n-1) (Alg. 1) for real and complex; for BIN add
+ * format: multiply by 2 (-1)^(n-1) (Alg. 1) for real and complex (PERM_F64X:
+ * the double-double sum, scaled exactly, as (hi, lo)); for BIN add
  * modulo 2^192, check that the low n-1 bits are zero (PERM_EINVAL otherwise),
  * shift them out, apply (-1)^(n-1) and check the value fits 128 bits
  * (PERM_EOVERFLOW otherwise).

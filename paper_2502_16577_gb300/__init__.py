@@ -19,10 +19,10 @@ import ctypes
 import numpy as np
 
 from . import _lib
-from ._lib import PERM_BIN, PERM_C128, PERM_EABORTED, PERM_F64, PermError, check, load
+from ._lib import PERM_BIN, PERM_C128, PERM_EABORTED, PERM_F64, PERM_F64X, PermError, check, load
 
 __all__ = ["perm", "perm_async", "perm_range", "perm_range_async", "perm_combine", "perm_sparse", "perm_sparse_async", "perm_host", "pipe_peaks", "BatchPlan", "AbortWord", "perm_grad", "perm_grad_async", "perm_grad_batched", "perm_grad_batched_async", "perm_grad_mixed", "permanent", "perm_type_of", "PermError",
-           "PERM_F64", "PERM_C128", "PERM_BIN", "PERM_EABORTED", "load"]
+           "PERM_F64", "PERM_C128", "PERM_BIN", "PERM_F64X", "perm_x", "PERM_EABORTED", "load"]
 
 
 def _torch():
@@ -76,12 +76,21 @@ def _u(words) -> int:
     return v
 
 
-def perm_async(A, out, status=None, stream=None) -> None:
+def _type_for(A, extended: bool) -> int:
+    t = perm_type_of(A.dtype)
+    if extended:
+        if t != PERM_F64:
+            raise TypeError("extended-precision products are for float64 matrices")
+        return PERM_F64X
+    return t
+
+
+def perm_async(A, out, status=None, stream=None, extended: bool = False) -> None:
     """Enqueue perm(A) on a stream without waiting; out / status are device tensors
-    (float64[1], float64[2] for complex, int64[2] for 0/1; int32[1])."""
+    (float64[1], float64[2] for complex or extended, int64[2] for 0/1; int32[1])."""
     lib = load()
     A = _as_device_matrix(A)
-    t = perm_type_of(A.dtype)
+    t = _type_for(A, extended)
     h, _ = _stream_handle(stream)
     rc = lib.perm(ctypes.c_void_p(A.data_ptr()), A.shape[0], t, ctypes.c_void_p(out.data_ptr()),
                   ctypes.c_void_p(status.data_ptr() if status is not None else 0), h)
@@ -106,12 +115,25 @@ def perm(A, stream=None):
     return _u(o)
 
 
-def perm_range_async(A, g_begin: int, g_end: int, out, status=None, stream=None) -> None:
+def perm_x(A, stream=None) -> tuple:
+    """Permanent of a float64 CUDA matrix with extended-precision products
+    (PERM_F64X): the unevaluated double-double (hi, lo).  Waits for it."""
+    A = _as_device_matrix(A)
+    out, status = _out_buffers(PERM_F64X, A.device, 2)
+    perm_async(A, out, status, stream, extended=True)
+    _, s = _stream_handle(stream)
+    s.synchronize()
+    check(int(status.item()), "perm")
+    o = out.cpu().numpy()
+    return float(o[0]), float(o[1])
+
+
+def perm_range_async(A, g_begin: int, g_end: int, out, status=None, stream=None, extended: bool = False) -> None:
     """Enqueue perm_range on a stream without waiting (out: float64[2] real,
     float64[4] complex, int64[3] for 0/1; status: int32[1])."""
     lib = load()
     A = _as_device_matrix(A)
-    t = perm_type_of(A.dtype)
+    t = _type_for(A, extended)
     h, _ = _stream_handle(stream)
     rc = lib.perm_range(ctypes.c_void_p(A.data_ptr()), A.shape[0], t, int(g_begin), int(g_end),
                         ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(status.data_ptr() if status is not None else 0),
@@ -119,13 +141,14 @@ def perm_range_async(A, g_begin: int, g_end: int, out, status=None, stream=None)
     check(rc, "perm_range")
 
 
-def perm_range(A, g_begin: int, g_end: int, stream=None):
-    """Raw partial over steps [g_begin, g_end): (hi, lo) for float64,
-    (re_hi, re_lo, im_hi, im_lo) for complex128, an int mod 2^192 for 0/1."""
+def perm_range(A, g_begin: int, g_end: int, stream=None, extended: bool = False):
+    """Raw partial over steps [g_begin, g_end): (hi, lo) for float64 (also with
+    extended products), (re_hi, re_lo, im_hi, im_lo) for complex128, an int
+    mod 2^192 for 0/1."""
     lib = load()
     A = _as_device_matrix(A)
-    t = perm_type_of(A.dtype)
-    words = {PERM_F64: 2, PERM_C128: 4, PERM_BIN: 3}[t]
+    t = _type_for(A, extended)
+    words = {PERM_F64: 2, PERM_F64X: 2, PERM_C128: 4, PERM_BIN: 3}[t]
     out, status = _out_buffers(t, A.device, words)
     h, s = _stream_handle(stream)
     rc = lib.perm_range(ctypes.c_void_p(A.data_ptr()), A.shape[0], t, int(g_begin), int(g_end),
@@ -153,7 +176,7 @@ def perm_combine(t: int, n: int, partials):
                 arr[i, w] = (v >> (64 * w)) & 0xFFFFFFFFFFFFFFFF
         out = np.zeros(2, dtype=np.uint64)
     else:
-        width = 2 if t == PERM_F64 else 4
+        width = 2 if t in (PERM_F64, PERM_F64X) else 4
         arr = np.ascontiguousarray(np.asarray(partials, dtype=np.float64).reshape(len(partials), width))
         out = np.zeros(1 if t == PERM_F64 else 2, dtype=np.float64)
     rc = lib.perm_combine(t, n, arr.ctypes.data_as(ctypes.c_void_p), len(partials), out.ctypes.data_as(ctypes.c_void_p))
@@ -162,6 +185,8 @@ def perm_combine(t: int, n: int, partials):
         return float(out[0])
     if t == PERM_C128:
         return complex(float(out[0]), float(out[1]))
+    if t == PERM_F64X:
+        return float(out[0]), float(out[1])
     return _u(out)
 
 
@@ -480,4 +505,6 @@ def perm_host(A, stream=None):
         return float(out[0])
     if t == PERM_C128:
         return complex(float(out[0]), float(out[1]))
+    if t == PERM_F64X:
+        return float(out[0]), float(out[1])
     return _u(out)

@@ -10,7 +10,7 @@ import os
 
 from . import build as _build
 
-PERM_F64, PERM_C128, PERM_BIN = 0, 1, 2
+PERM_F64, PERM_C128, PERM_BIN, PERM_F64X = 0, 1, 2, 3
 PERM_OK, PERM_EINVAL, PERM_ERANGE, PERM_EOVERFLOW, PERM_ECUDA, PERM_ENOMEM, PERM_EABORTED = range(7)
 
 _vp = ctypes.c_void_p

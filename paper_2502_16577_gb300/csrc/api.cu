@@ -153,6 +153,8 @@ static KernelEntry dense_entry(int type, int n) {
       return n <= 24 ? cplx_lo_entry(n) : cplx_hi_entry(n);
     case PERM_BIN:
       return n <= 32 ? bin_lo_entry(n) : bin_hi_entry(n);
+    case PERM_F64X:
+      return n <= 32 ? realx_entry_lo(n) : realx_entry_hi(n);
     default:
       return {nullptr, 0};
   }
@@ -160,7 +162,8 @@ static KernelEntry dense_entry(int type, int n) {
 
 static size_t partial_bytes(int type) {
   switch (type) {
-    case PERM_F64: return sizeof(dd);
+    case PERM_F64:
+    case PERM_F64X: return sizeof(dd);
     case PERM_C128: return 2 * sizeof(dd);
     default: return 8 * sizeof(uint32_t);
   }
@@ -173,10 +176,11 @@ __global__ void write_trivial_kernel(int type, int mode, void* out, int32_t* sta
     double* o = static_cast<double*>(out);
     if (mode == 0) o[0] = 1.0;
     else o[0] = o[1] = 0.0;
-  } else if (type == PERM_C128) {
+  } else if (type == PERM_C128 || type == PERM_F64X) {
     double* o = static_cast<double*>(out);
     if (mode == 0) { o[0] = 1.0; o[1] = 0.0; }
-    else o[0] = o[1] = o[2] = o[3] = 0.0;
+    else if (type == PERM_C128) o[0] = o[1] = o[2] = o[3] = 0.0;
+    else o[0] = o[1] = 0.0;
   } else {
     uint64_t* o = static_cast<uint64_t*>(out);
     if (mode == 0) { o[0] = 1; o[1] = 0; }
@@ -274,7 +278,7 @@ const char* perm_status_string(int status) {
 }
 
 static int check_common(const void* A, int n, int type, const void* out) {
-  if (type != PERM_F64 && type != PERM_C128 && type != PERM_BIN) return PERM_EINVAL;
+  if (type != PERM_F64 && type != PERM_C128 && type != PERM_BIN && type != PERM_F64X) return PERM_EINVAL;
   if (n < 0 || n > PERM_NMAX) return PERM_ERANGE;
   if (!out || (n > 0 && !A)) return PERM_EINVAL;
   return PERM_OK;
@@ -320,6 +324,21 @@ int perm_combine(int type, int n, const void* partials, int count, void* out) {
     }
     return PERM_OK;
   }
+  if (type == PERM_F64X) {
+    const double* p = static_cast<const double*>(partials);
+    double* o = static_cast<double*>(out);
+    if (n == 0) {
+      o[0] = 1.0;
+      o[1] = 0.0;
+      return PERM_OK;
+    }
+    hdd acc = {0.0, 0.0};
+    for (int i = 0; i < count; ++i) acc = hdd_add(acc, hdd{p[2 * (size_t)i], p[2 * (size_t)i + 1]});
+    const double f = (n & 1) ? 2.0 : -2.0;  // exact on both words
+    o[0] = acc.hi * f;
+    o[1] = acc.lo * f;
+    return PERM_OK;
+  }
   if (type == PERM_BIN) {
     const uint64_t* p = static_cast<const uint64_t*>(partials);
     uint64_t* o = static_cast<uint64_t*>(out);
@@ -362,7 +381,9 @@ int perm_host(const void* A_host, int n, int type, void* out_host, void* stream)
   int rc = check_common(A_host, n, type, out_host);
   if (rc) return rc;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  size_t elem = type == PERM_F64 ? sizeof(double) : type == PERM_C128 ? 2 * sizeof(double) : sizeof(uint8_t);
+  size_t elem = (type == PERM_F64 || type == PERM_F64X) ? sizeof(double)
+                : type == PERM_C128                      ? 2 * sizeof(double)
+                                                         : sizeof(uint8_t);
   size_t in_bytes = elem * (size_t)n * (size_t)n;
   size_t out_bytes = type == PERM_F64 ? sizeof(double) : 2 * sizeof(uint64_t);
   void* dA = nullptr;

@@ -19,6 +19,8 @@ KernelEntry bin_lo_entry(int n);    // n = 1..32
 KernelEntry bin_hi_entry(int n);    // n = 33..63
 KernelEntry cplx_lo_entry(int n);   // n = 1..24
 KernelEntry cplx_hi_entry(int n);   // n = 25..63
+KernelEntry realx_entry_lo(int n);  // n = 1..32, extended products
+KernelEntry realx_entry_hi(int n);  // n = 33..63
 
 // Device view of the word registered with perm_set_abort_word, or null (api.cu).
 const volatile uint32_t* current_abort_word();

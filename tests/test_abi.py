@@ -71,6 +71,8 @@ def test_host_argument_checks_need_no_gpu(lib):
     assert lib.perm(dummy, 64, 0, dummy, vp(0), vp(0)) == 2    # n > 63
     assert lib.perm(dummy, -1, 0, dummy, vp(0), vp(0)) == 2
     assert lib.perm(dummy, 5, 7, dummy, vp(0), vp(0)) == 1     # bad type
+    assert lib.perm(dummy, 5, 4, dummy, vp(0), vp(0)) == 1     # first type past PERM_F64X
+    assert lib.perm(dummy, 64, 3, dummy, vp(0), vp(0)) == 2    # PERM_F64X, n > 63
     assert lib.perm(vp(0), 5, 0, dummy, vp(0), vp(0)) == 1     # null A
     assert lib.perm(dummy, 5, 0, vp(0), vp(0), vp(0)) == 1     # null out
     assert lib.perm_range(dummy, 5, 0, 3, 2, dummy, vp(0), vp(0)) == 2   # begin > end
@@ -87,6 +89,27 @@ def test_combine_real_partials(oracle):
         parts = [oracle.ryser_f64_range(A, a, b) for a, b in zip(cuts[:-1], cuts[1:])]
         got = pg.perm_combine(pg.PERM_F64, n, parts)
         assert got == pytest.approx(oracle.perm_dp_f64(A), abs=1e-13 * oracle.perm_dp_f64(np.abs(A)))
+
+
+def test_combine_extended_partials_stay_double_double(oracle):
+    """PERM_F64X partials (same layout as PERM_F64) combine into an unevaluated
+    (hi, lo) scaled exactly by 2 (-1)^(n-1); the oracle's double-double range
+    sums stand in for the kernel's partials."""
+    from fractions import Fraction
+
+    import paper_2502_16577_gb300 as pg
+
+    for n in (1, 6, 11):
+        A = syn.signed_real(n, 60 + n)
+        N = 2 ** (n - 1)
+        cuts = sorted({0, N, N // 3, N // 2})
+        parts = [oracle.ryser_dd_range(A, a, b) for a, b in zip(cuts[:-1], cuts[1:])]
+        hi, lo = pg.perm_combine(pg.PERM_F64X, n, parts)
+        assert hi + lo == hi
+        exact = oracle.perm_bruteforce(A) if n <= 8 else sum(map(Fraction, oracle.perm_dd(A)))
+        assert abs(Fraction(hi) + Fraction(lo) - exact) <= Fraction(1, 10 ** 26) * Fraction(
+            oracle.perm_dp_f64(np.abs(A)))
+    assert pg.perm_combine(pg.PERM_F64X, 0, []) == (1.0, 0.0)
 
 
 def test_combine_complex_partials(oracle):
