@@ -364,20 +364,30 @@ def run_gpu(args):
 def measure_batched(pg, dev, stream, count: int = 8192):
     """Batched boson workload: 8192 complex k x k submatrices (k uniform in
     8..26, rows with replacement from a Haar 256 x 256 unitary): one graph
-    replay of the batched plan vs a loop of perm() launches on one stream."""
+    replay of the batched plan, with the drawn modes as row labels (repeated
+    rows summed over their multiplicities) and without them, vs a loop of
+    perm() launches on one stream."""
     import torch
 
-    mats = syn.batched_boson(count)
-    plan = pg.BatchPlan(mats, device=dev)
-    plan.run(stream)  # warm-up
+    mats, rows = syn.batched_boson(count, with_rows=True)
     ev = lambda: torch.cuda.Event(enable_timing=True)
     e0, e1 = ev(), ev()
-    e0.record(stream)
-    plan.run_async(stream)
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    t_graph = e0.elapsed_time(e1) * 1e-3
-    res = plan.run(stream)
+
+    def replay(plan):
+        plan.run(stream)  # warm-up
+        e0.record(stream)
+        plan.run_async(stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        t = e0.elapsed_time(e1) * 1e-3
+        return t, plan.run(stream)
+
+    plan = pg.BatchPlan(mats, device=dev)
+    t_plain, res = replay(plan)
+    plan.close()
+    plan = pg.BatchPlan(mats, device=dev, row_labels=rows)
+    t_graph, res_lab = replay(plan)
+    plan.close()
     devm = [torch.from_numpy(np.ascontiguousarray(m)).to(dev) for m in mats]
     out = torch.zeros(2 * count, dtype=torch.float64, device=dev)
     st = torch.zeros(count, dtype=torch.int32, device=dev)
@@ -392,11 +402,13 @@ def measure_batched(pg, dev, stream, count: int = 8192):
     t_loop = e0.elapsed_time(e1) * 1e-3
     o = out.cpu().numpy()
     same = bool(np.array_equal(res, o[0::2] + 1j * o[1::2]))
-    plan.close()
+    scale = np.maximum(np.abs(res), 1e-300)
     steps = sum(1 << (m.shape[0] - 1) for m in mats)
-    return {"workload": f"{count} complex128 boson submatrices, k uniform 8..26", "perms_per_s": count / t_graph,
-            "steps_per_s": steps / t_graph, "loop_perms_per_s": count / t_loop, "speedup_vs_loop": t_loop / t_graph,
-            "identical_to_loop": same, "launches_per_replay": 3}
+    return {"workload": f"{count} complex128 boson submatrices, k uniform 8..26, drawn modes as row labels",
+            "perms_per_s": count / t_graph, "plain_perms_per_s": count / t_plain,
+            "steps_per_s": steps / t_plain, "loop_perms_per_s": count / t_loop,
+            "speedup_vs_loop": t_loop / t_graph, "labeled_vs_plain_max_rel": float(np.max(np.abs(res_lab - res) / scale)),
+            "plain_identical_to_loop": same, "launches_per_replay": 3}
 
 
 def measure_grad(pg, dev, stream, reps: int = 3):

@@ -166,6 +166,15 @@ int perm_sparse(int n, const int32_t* cptrs, const int32_t* rids, const double* 
  *     status     device int32[count] or NULL (perm() status per matrix).
  *   A_packed, out and status are bound to the plan: every perm_batched()
  *   replay reads and writes these buffers.
+ * perm_batched_plan_create_labeled - the same, with row_labels_host (host
+ *   int32[sum of ns], the rows of matrix 0, then matrix 1, ...): rows of one
+ *   matrix with equal labels must be equal (checked on the device: PERM_EINVAL
+ *   in its status otherwise).  A matrix whose distinct rows occur mu_r times
+ *   is then summed over the multiplicities (Glynn's form of Eq. 2 grouped by
+ *   the number of copies of each row with sign -1, weights C(mu_r, k_r)),
+ *   1/2 prod_r (mu_r + 1) terms instead of 2^(k-1); results agree with the
+ *   unlabelled plan to the accuracy of the kernels, not bitwise.
+ *   row_labels_host NULL: PERM_EINVAL.
  * perm_batched - replay the plan's graph on stream (allocates nothing).
  * perm_batched_autotune - time the candidate chunk exponents and the
  *   one-matrix-per-lane mode of every size class on the plan's own matrices
@@ -178,6 +187,9 @@ int perm_sparse(int n, const int32_t* cptrs, const int32_t* rids, const double* 
 typedef struct perm_batch_plan perm_batch_plan;
 int perm_batched_plan_create(perm_batch_plan** plan, int type, const int* ns_host, int count, const void* A_packed,
                              const int64_t* offsets_host, void* out, int32_t* status);
+int perm_batched_plan_create_labeled(perm_batch_plan** plan, int type, const int* ns_host, int count,
+                                     const void* A_packed, const int64_t* offsets_host, void* out, int32_t* status,
+                                     const int32_t* row_labels_host);
 int perm_batched(perm_batch_plan* plan, void* stream);
 int perm_batched_autotune(perm_batch_plan* plan, int rounds, void* stream);
 int perm_batched_plan_info(const perm_batch_plan* plan, int k, int* mode, int* c, int* nitems);

@@ -400,9 +400,15 @@ class BatchPlan:
     input is real and dtype="float64").
 
     The matrices are packed into one device buffer owned by the plan; run()
-    replays the captured graph (one launch) and returns the device results."""
+    replays the captured graph (one launch) and returns the device results.
 
-    def __init__(self, mats, device=None, autotune_rounds: int = 0, stream=None, dtype="complex128"):
+    row_labels (optional): one integer sequence per matrix, equal labels
+    marking equal rows (e.g. the modes a boson-sampling submatrix was drawn
+    from); such matrices are summed over row multiplicities, with fewer
+    terms.  Labelled rows are checked for equality on the device."""
+
+    def __init__(self, mats, device=None, autotune_rounds: int = 0, stream=None, dtype="complex128",
+                 row_labels=None):
         torch = _torch()
         lib = load()
         device = device or torch.device("cuda")
@@ -426,10 +432,21 @@ class BatchPlan:
         self._plan = ctypes.c_void_p(0)
         karr = (ctypes.c_int * len(ks))(*ks)
         oarr = (ctypes.c_int64 * len(ks))(*offs)
-        check(lib.perm_batched_plan_create(ctypes.byref(self._plan), self.type, karr, len(ks),
-                                           ctypes.c_void_p(self.A.data_ptr()), oarr,
-                                           ctypes.c_void_p(self.out.data_ptr()),
-                                           ctypes.c_void_p(self.status.data_ptr())), "perm_batched_plan_create")
+        if row_labels is None:
+            check(lib.perm_batched_plan_create(ctypes.byref(self._plan), self.type, karr, len(ks),
+                                               ctypes.c_void_p(self.A.data_ptr()), oarr,
+                                               ctypes.c_void_p(self.out.data_ptr()),
+                                               ctypes.c_void_p(self.status.data_ptr())), "perm_batched_plan_create")
+        else:
+            if len(row_labels) != len(ks) or any(len(l) != k for l, k in zip(row_labels, ks)):
+                raise ValueError("row_labels needs one label per row of every matrix")
+            flat = np.ascontiguousarray(np.concatenate([np.asarray(l, dtype=np.int32) for l in row_labels]))
+            larr = flat.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+            check(lib.perm_batched_plan_create_labeled(ctypes.byref(self._plan), self.type, karr, len(ks),
+                                                       ctypes.c_void_p(self.A.data_ptr()), oarr,
+                                                       ctypes.c_void_p(self.out.data_ptr()),
+                                                       ctypes.c_void_p(self.status.data_ptr()), larr),
+                  "perm_batched_plan_create_labeled")
         if autotune_rounds:
             h, _ = _stream_handle(stream)
             check(lib.perm_batched_autotune(self._plan, int(autotune_rounds), h), "perm_batched_autotune")

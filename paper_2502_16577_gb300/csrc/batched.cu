@@ -21,6 +21,17 @@
 //  * Every item writes its partial to its own slot; the finish kernel adds a
 //    matrix's slots in a fixed order (deterministic), scales by 2 (-1)^(k-1)
 //    and writes the result.  Execution allocates nothing.
+//  * Repeated rows (boson-sampling submatrices drawn with replacement): when
+//    the caller labels equal rows, a matrix whose distinct rows rho occur
+//    mu_rho times is swept in its transposed form.  Glynn's form of Eq. 2,
+//    perm = 2^(1-k) sum_{d, d_f = 1} prod_r d_r prod_j sum_r d_r a_rj, is
+//    grouped by the number k_rho of copies of each row with d = -1: the
+//    copies contribute (mu_rho - 2 k_rho) row_rho to every column sum, with
+//    weight C(mu_rho, k_rho) (-1)^(k_rho).  One copy of a singleton row is
+//    fixed at d = +1, the other singletons are the Gray-code bits, and each
+//    combination (k_rho) of the repeated rows is one ordinary sweep with a
+//    shifted base vector and a weight applied when the slots are added:
+//    1/2 prod_rho (mu_rho + 1) terms instead of 2^(k-1).
 #include <math.h>
 #include <stdint.h>
 #include <string.h>
@@ -39,13 +50,30 @@ namespace permgpu {
 constexpr int kBatchKMax = 32;
 constexpr int kLaneMode = 1, kWarpMode = 0;
 
+// One sweep unit: a matrix, or one multiplicity combination of a matrix with
+// repeated rows.
 struct BatchMat {
   int32_t k;
   int32_t sum_s;
-  int32_t flags;  // 1: non-finite entry, 2: zero row, 4: exponent range
-  int32_t slot0;  // first partial slot of this matrix
+  int32_t flags;  // 1: non-finite entry or unequal labelled rows, 2: zero row, 4: exponent range
+  int32_t slot0;  // first partial slot of this unit
   int64_t a_off;  // element offset of the matrix in the packed input
   int64_t d_off;  // longlong2 offset of its table (D, base, zero) in the plan
+  int32_t g;      // Gray bits of the sweep: k - 1 for a plain matrix
+  int32_t desc;   // -1: plain (rows of A are the factors); else the unit's descriptor
+};
+
+// Descriptor of a transposed unit (ints, host-built): the fixed row f, the G
+// toggled rows, R (row, coefficient) pairs of the repeated rows, and P row
+// pairs that must be equal: f, G, t_0..t_{G-1}, R, (r, c) x R, P, (a, b) x P.
+// The factors are the columns of A.
+
+// One output matrix: its units and its slots (contiguous).
+struct BatchOut {
+  int32_t k;
+  int32_t u0, nu;
+  int32_t slot0, nslots;
+  int32_t pad;
 };
 
 struct BatchItem {
@@ -60,7 +88,10 @@ struct BatchItem {
 
 struct BatchArgs {
   const double* A;        // packed (re, im) pairs
-  const BatchMat* mats;
+  const BatchMat* mats;   // units
+  const BatchOut* outs;   // output matrices
+  const int32_t* desc;    // descriptors of transposed units
+  const double* slot_w;   // weight of every slot's partial
   const BatchItem* items;
   const int32_t* lane_mats;
   longlong2* table;
@@ -68,15 +99,92 @@ struct BatchArgs {
   unsigned int* counter;
   double* out;            // (re, im) per matrix
   int32_t* status;        // per matrix (optional)
-  int nmats;
+  int nmats;              // output matrices
+  int nunits;
   int nitems;
   int type;               // PERM_C128 or PERM_F64
 };
 
-// One CTA per matrix: D[(2j+s) k + i], base[k], zero[k] as in cplx_stage.
+// Transposed unit: factor i is column i of A; the toggles are rows, the
+// base holds the fixed row and the repeated rows times their coefficients.
+// Scales, rounding and the odd fixed row (real) follow the plain branch.
+__device__ void batch_prep_transposed(const BatchArgs& a, const BatchMat& bm, int& s_sum, int& s_bound,
+                                      int& s_flags) {
+  const int k = bm.k;
+  const int32_t* d = a.desc + bm.desc;
+  const int f = d[0], G = d[1];
+  const int32_t* tg = d + 2;
+  const int R = d[2 + G];
+  const int32_t* rp = d + 3 + G;
+  const int P = rp[2 * R];
+  const int32_t* pp = rp + 2 * R + 1;
+  const int i = threadIdx.x;
+  if (i >= k) return;
+  const bool real = a.type == PERM_F64;
+  const int w = real ? 1 : 2;
+  const double* col = a.A + (int64_t)w * (bm.a_off + i);  // entry (r, i) at col[w r k]
+  double absum = 0.0;
+  int fin = 1;
+  for (int r = 0; r < k; ++r)
+    for (int q = 0; q < w; ++q) {
+      const double v = col[(int64_t)w * r * k + q];
+      fin &= isfinite(v) ? 1 : 0;
+      absum += fabs(v);
+    }
+  int bad = 0;
+  for (int t = 0; t < P; ++t)
+    for (int q = 0; q < w; ++q)
+      bad |= col[(int64_t)w * pp[2 * t] * k + q] != col[(int64_t)w * pp[2 * t + 1] * k + q];
+  int kk = 0;
+  if (fin && absum > 0.0) frexp(absum, &kk);
+  if (real) {
+    long long* RD = reinterpret_cast<long long*>(a.table + bm.d_off);
+    long long* rbase = RD + (size_t)2 * (k > 1 ? k - 1 : 0) * k;
+    const int s = 61 - kk;
+    auto q_of = [&](int r) { return fin ? __double2ll_rn(ldexp(col[(int64_t)r * k], s - 1)) : 0ll; };
+    long long b = fin ? 2 * __double2ll_rd(ldexp(col[(int64_t)f * k], s - 1)) + 1 : 1;
+    for (int j = 0; j < k - 1; ++j) {
+      const long long q = j < G ? q_of(tg[j]) : 0;
+      b -= 2 * q;
+      RD[(2 * j) * k + i] = 4 * q;
+      RD[(2 * j + 1) * k + i] = -4 * q;
+    }
+    for (int t = 0; t < R; ++t) b += (long long)rp[2 * t + 1] * 2 * q_of(rp[2 * t]);
+    rbase[i] = b;
+    rbase[k + i] = 0;
+    atomicAdd(&s_sum, s);
+  } else {
+    longlong2* D = a.table + bm.d_off;
+    longlong2* base = D + (size_t)2 * (k > 1 ? k - 1 : 0) * k;
+    const int s = 60 - kk;
+    auto q_of = [&](int r, int part) {
+      return fin ? __double2ll_rn(ldexp(col[(int64_t)2 * r * k + part], s)) : 0ll;
+    };
+    long long br = q_of(f, 0), bi = q_of(f, 1);
+    for (int j = 0; j < k - 1; ++j) {
+      const long long qr = j < G ? q_of(tg[j], 0) : 0, qi = j < G ? q_of(tg[j], 1) : 0;
+      br -= qr;
+      bi -= qi;
+      D[(2 * j) * k + i] = make_longlong2(2 * qr, 2 * qi);
+      D[(2 * j + 1) * k + i] = make_longlong2(-2 * qr, -2 * qi);
+    }
+    for (int t = 0; t < R; ++t) {
+      br += (long long)rp[2 * t + 1] * q_of(rp[2 * t], 0);
+      bi += (long long)rp[2 * t + 1] * q_of(rp[2 * t], 1);
+    }
+    base[i] = make_longlong2(br, bi);
+    base[k + i] = make_longlong2(0, 0);
+    atomicAdd(&s_sum, s);
+  }
+  atomicAdd(&s_bound, kk - 1);
+  if (!fin || bad) atomicOr(&s_flags, 1);
+  if (fin && absum == 0.0) atomicOr(&s_flags, 2);
+}
+
+// One CTA per unit: D[(2j+s) k + i], base[k], zero[k] as in cplx_stage.
 __global__ void __launch_bounds__(kBlock) batch_prep_kernel(BatchArgs a) {
   const int m = blockIdx.x;
-  if (m >= a.nmats) return;
+  if (m >= a.nunits) return;
   const BatchMat bm = a.mats[m];
   const int k = bm.k;
   longlong2* D = a.table + bm.d_off;
@@ -90,7 +198,9 @@ __global__ void __launch_bounds__(kBlock) batch_prep_kernel(BatchArgs a) {
   }
   __syncthreads();
   const int i = threadIdx.x;
-  if (a.type == PERM_F64) {
+  if (bm.desc >= 0) {
+    batch_prep_transposed(a, bm, s_sum, s_bound, s_flags);
+  } else if (a.type == PERM_F64) {
     // real: odd fixed-point rows as in real_stage (Y = 2 x 2^s)
     long long* RD = reinterpret_cast<long long*>(a.table + bm.d_off);
     long long* rbase = RD + (size_t)2 * (k > 1 ? k - 1 : 0) * k;
@@ -291,7 +401,7 @@ __device__ __forceinline__ void batch_item_real(const BatchArgs& a, const BatchI
     const BatchMat bm = a.mats[m];
     const bool ok = active && bm.flags == 0;
     if constexpr (K <= 16)  // one matrix per lane only for short sweeps (as complex)
-      batch_sweep_real<K>(reinterpret_cast<const long long*>(a.table + bm.d_off), bm.sum_s, K - 1, 0ull, ok, acc);
+      batch_sweep_real<K>(reinterpret_cast<const long long*>(a.table + bm.d_off), bm.sum_s, bm.g, 0ull, ok, acc);
     if (active) {
       a.slots[2 * bm.slot0] = acc;
       a.slots[2 * bm.slot0 + 1] = zero;
@@ -299,7 +409,7 @@ __device__ __forceinline__ void batch_item_real(const BatchArgs& a, const BatchI
   } else {
     const BatchMat bm = a.mats[it.mat];
     const uint64_t chunk = (uint64_t)it.chunk0 + lane;
-    const uint64_t nchunks = 1ull << (K - 1 - it.c);
+    const uint64_t nchunks = 1ull << (bm.g - it.c);
     const bool active = chunk < nchunks && bm.flags == 0;
     batch_sweep_real<K>(reinterpret_cast<const long long*>(a.table + bm.d_off), bm.sum_s, it.c,
                         (active ? chunk : 0ull) << it.c, active, acc);
@@ -401,7 +511,7 @@ __device__ __forceinline__ void batch_item(const BatchArgs& a, const BatchItem& 
     const bool ok = active && bm.flags == 0;
     // one complex matrix per lane only for short sweeps (K <= 16, enforced by
     // the plan): longer rows would not fit the registers of a lane
-    if constexpr (K <= 16) batch_sweep<K>(a.table + bm.d_off, bm.sum_s, K - 1, 0ull, ok, accr, acci);
+    if constexpr (K <= 16) batch_sweep<K>(a.table + bm.d_off, bm.sum_s, bm.g, 0ull, ok, accr, acci);
     if (active) {
       a.slots[2 * bm.slot0] = accr;
       a.slots[2 * bm.slot0 + 1] = acci;
@@ -409,7 +519,7 @@ __device__ __forceinline__ void batch_item(const BatchArgs& a, const BatchItem& 
   } else {
     const BatchMat bm = a.mats[it.mat];
     const uint64_t chunk = (uint64_t)it.chunk0 + (K >= 16 ? (lane >> 1) : lane);
-    const uint64_t nchunks = 1ull << (K - 1 - it.c);
+    const uint64_t nchunks = 1ull << (bm.g - it.c);
     const bool active = chunk < nchunks && bm.flags == 0;
     if constexpr (K >= 16)
       batch_sweep2<K>(a.table + bm.d_off, bm.sum_s, it.c, (active ? chunk : 0ull) << it.c, active, accr, acci);
@@ -458,16 +568,31 @@ __global__ void __launch_bounds__(kBlock, 2) batch_main_kernel(BatchArgs a) {
   }
 }
 
-// One thread per matrix: its slots in order, then the factor 2 (-1)^(k-1).
-__global__ void batch_finish_kernel(BatchArgs a, const int32_t* nslots) {
+// v * w for a small integer weight w (exact product of the head by FMA).
+__device__ __forceinline__ dd dd_scale(dd v, double w) {
+  const double p = v.hi * w;
+  const double e = fma(v.hi, w, -p) + v.lo * w;
+  return dd_make(p, e);
+}
+
+// One thread per matrix: its slots in order (times their unit's weight),
+// then the factor 2 (-1)^(k-1).
+__global__ void batch_finish_kernel(BatchArgs a) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= a.nmats) return;
-  const BatchMat bm = a.mats[m];
+  const BatchOut bo = a.outs[m];
+  int flags = 0;
+  for (int u = bo.u0; u < bo.u0 + bo.nu; ++u) flags |= a.mats[u].flags;
+  // the units of one matrix share their scales, so flags 2 (a zero row, or
+  // for transposed units a zero column: perm = 0) and 4 agree between them
   dd r = {0.0, 0.0}, im = {0.0, 0.0};
-  for (int s = 0; s < nslots[m]; ++s) {
-    r = dd_add(r, a.slots[2 * (bm.slot0 + s)]);
-    im = dd_add(im, a.slots[2 * (bm.slot0 + s) + 1]);
+  for (int s = bo.slot0; s < bo.slot0 + bo.nslots; ++s) {
+    const double w = a.slot_w[s];
+    const dd sr = a.slots[2 * s], si = a.slots[2 * s + 1];
+    r = dd_add(r, w == 1.0 ? sr : dd_scale(sr, w));
+    im = dd_add(im, w == 1.0 ? si : dd_scale(si, w));
   }
+  const BatchMat bm = {bo.k, 0, flags, 0, 0, 0, 0, 0};
   const double f = (bm.k & 1) ? 2.0 : -2.0;
   const double nan = __longlong_as_double(0x7ff8000000000000ll);
   int32_t st = PERM_OK;
@@ -500,6 +625,8 @@ struct perm_batch_plan {
   int max_k = 0;
   std::vector<int> ks;
   std::vector<int64_t> a_off;
+  std::vector<int32_t> labels;   // row labels, sum of ks entries (empty: all rows distinct)
+  std::vector<int64_t> lab_off;  // first label of every matrix
   // per size class: mode and chunk exponent
   int cls_mode[kBatchKMax + 1];
   int cls_c[kBatchKMax + 1];
@@ -507,11 +634,14 @@ struct perm_batch_plan {
   BatchMat* d_mats = nullptr;
   BatchItem* d_items = nullptr;
   int32_t* d_lane_mats = nullptr;
-  int32_t* d_nslots = nullptr;
+  BatchOut* d_outs = nullptr;
+  int32_t* d_desc = nullptr;
+  double* d_slot_w = nullptr;
   longlong2* d_table = nullptr;
   dd* d_slots = nullptr;
   unsigned int* d_counter = nullptr;
   int nitems = 0;
+  int nunits = 0;
   int nslots_total = 0;
   size_t table_elems = 0;
   // bound buffers and the captured graph
@@ -529,7 +659,9 @@ static void batch_free(perm_batch_plan* p) {
   cudaFree(p->d_mats);
   cudaFree(p->d_items);
   cudaFree(p->d_lane_mats);
-  cudaFree(p->d_nslots);
+  cudaFree(p->d_outs);
+  cudaFree(p->d_desc);
+  cudaFree(p->d_slot_w);
   cudaFree(p->d_table);
   cudaFree(p->d_slots);
   cudaFree(p->d_counter);
@@ -537,7 +669,10 @@ static void batch_free(perm_batch_plan* p) {
 }
 
 // Default choice per size class: one matrix per lane while a sweep is short,
-// otherwise chunks of 2^c steps with at least ~8 warp items per matrix.
+// otherwise chunks of 2^c steps with at least ~8 warp items per matrix, and
+// c <= 12: a warp item is then at most 2^17 steps, a few ms of one warp, so
+// the last wave of the queue stays short (with c = k - 9 a k = 26 item ran
+// for about 0.4 s, and how full its last wave was decided the run time).
 static void batch_default_classes(perm_batch_plan* p) {
   for (int k = 0; k <= kBatchKMax; ++k) {
     if (k <= 14) {
@@ -546,6 +681,7 @@ static void batch_default_classes(perm_batch_plan* p) {
     } else {
       p->cls_mode[k] = kWarpMode;
       int c = k - 1 - 5 - 3;  // 32 chunks per item, 8 items per matrix
+      if (c > 12) c = 12;
       if (c < 6) c = 6;
       if (c > k - 1) c = k - 1;
       p->cls_c[k] = c;
@@ -553,62 +689,169 @@ static void batch_default_classes(perm_batch_plan* p) {
   }
 }
 
-// Build the work queue, slots and matrix records for the current class
+// Sweep units of one matrix.  Without repeated labels: the matrix itself
+// (g = k - 1, weight 1).  With them: the transposed sweeps of the grouped
+// Glynn sum (see the top of this file), when they have fewer terms.
+struct UnitPlan {
+  int g;
+  double w;
+  std::vector<int32_t> desc;  // empty: plain
+};
+
+static void plan_units(const perm_batch_plan* p, int m, std::vector<UnitPlan>& units) {
+  const int k = p->ks[m];
+  units.clear();
+  UnitPlan plain{k - 1, 1.0, {}};
+  if (p->labels.empty() || k < 2) {
+    units.push_back(plain);
+    return;
+  }
+  // groups of equal labels, in order of first appearance
+  std::vector<int32_t> lab(p->labels.begin() + p->lab_off[m], p->labels.begin() + p->lab_off[m] + k);
+  std::vector<std::vector<int>> groups;
+  for (int r = 0; r < k; ++r) {
+    size_t gi = 0;
+    while (gi < groups.size() && lab[groups[gi][0]] != lab[r]) ++gi;
+    if (gi == groups.size()) groups.emplace_back();
+    groups[gi].push_back(r);
+  }
+  if ((int)groups.size() == k) {
+    units.push_back(plain);
+    return;
+  }
+  // fix one copy of a singleton row if there is one, else of the smallest group
+  size_t fx = 0;
+  for (size_t gi = 0; gi < groups.size(); ++gi)
+    if (groups[gi].size() < groups[fx].size()) fx = gi;
+  std::vector<int> tog;
+  std::vector<std::pair<int, int>> repd;  // (row, multiplicity)
+  std::vector<std::pair<int, int>> pairs;
+  for (size_t gi = 0; gi < groups.size(); ++gi) {
+    const int mu = (int)groups[gi].size() - (gi == fx ? 1 : 0);
+    const int r0 = groups[gi][0];
+    if (mu == 1) tog.push_back(r0);
+    else if (mu >= 2) repd.push_back({r0, mu});
+    for (size_t t = 1; t < groups[gi].size(); ++t) pairs.push_back({r0, groups[gi][t]});
+  }
+  const int G = (int)tog.size();
+  double combos = 1.0;
+  for (auto& rm : repd) combos *= rm.second + 1;
+  if (std::ldexp(combos, G) >= std::ldexp(1.0, k - 1)) {
+    units.push_back(plain);
+    return;
+  }
+  // every combination (k_rho) of the repeated rows: coefficient mu - 2 k_rho,
+  // weight prod C(mu, k_rho) (-1)^(k_rho); times (-1)^(G - (k-1)) for the
+  // sign of the toggled rows against the plain sweep's 2 (-1)^(k-1)
+  std::vector<int> kr(repd.size(), 0);
+  for (bool first = true;; first = false) {
+    UnitPlan u;
+    u.g = G;
+    double w = ((G - (k - 1)) & 1) ? -1.0 : 1.0;
+    u.desc.push_back(groups[fx][0]);
+    u.desc.push_back(G);
+    for (int t : tog) u.desc.push_back(t);
+    u.desc.push_back((int32_t)repd.size());
+    for (size_t t = 0; t < repd.size(); ++t) {
+      const int mu = repd[t].second;
+      u.desc.push_back(repd[t].first);
+      u.desc.push_back(mu - 2 * kr[t]);
+      double c = 1.0;
+      for (int q = 0; q < kr[t]; ++q) c = c * (mu - q) / (q + 1);
+      w *= (kr[t] & 1) ? -c : c;
+    }
+    const size_t np = first ? pairs.size() : 0;  // equality checks once per matrix
+    u.desc.push_back((int32_t)np);
+    for (size_t t = 0; t < np; ++t) {
+      u.desc.push_back(pairs[t].first);
+      u.desc.push_back(pairs[t].second);
+    }
+    u.w = w;
+    units.push_back(std::move(u));
+    size_t t = 0;
+    while (t < repd.size() && ++kr[t] > repd[t].second) kr[t++] = 0;
+    if (t == repd.size()) break;
+  }
+}
+
+// Build the sweep units, work queue, slots and records for the current class
 // choices (host), and upload them.
 static int batch_build(perm_batch_plan* p) {
-  std::vector<BatchMat> mats(p->count);
-  std::vector<int32_t> nslots(p->count, 0);
+  struct Unit {
+    int m, g, combo;
+    double w;
+    std::vector<int32_t> desc;
+  };
+  std::vector<Unit> all;
+  std::vector<UnitPlan> ups;
+  for (int m = 0; m < p->count; ++m) {
+    plan_units(p, m, ups);
+    for (size_t c = 0; c < ups.size(); ++c) all.push_back({m, ups[c].g, (int)c, ups[c].w, std::move(ups[c].desc)});
+  }
+  // units of one size and Gray length together, then by matrix: the units
+  // (and slots) of every matrix are contiguous
+  std::stable_sort(all.begin(), all.end(), [&](const Unit& x, const Unit& y) {
+    const int kx = p->ks[x.m], ky = p->ks[y.m];
+    if (kx != ky) return kx < ky;
+    if (x.g != y.g) return x.g < y.g;
+    return x.m < y.m;
+  });
+  const int nu = (int)all.size();
+  std::vector<BatchMat> mats(nu);
+  std::vector<BatchOut> outs(p->count);
+  std::vector<int32_t> desc;
+  std::vector<double> slot_w;
   std::vector<BatchItem> items;
   std::vector<int32_t> lane_mats;
   size_t toff = 0;
-  for (int m = 0; m < p->count; ++m) {
-    const int k = p->ks[m];
-    mats[m].k = k;
-    mats[m].sum_s = 0;
-    mats[m].flags = 0;
-    mats[m].a_off = p->a_off[m];
-    mats[m].d_off = (int64_t)toff;
+  for (int u = 0; u < nu; ++u) {
+    const int k = p->ks[all[u].m];
+    mats[u].k = k;
+    mats[u].sum_s = 0;
+    mats[u].flags = 0;
+    mats[u].a_off = p->a_off[all[u].m];
+    mats[u].d_off = (int64_t)toff;
+    mats[u].g = all[u].g;
+    mats[u].desc = all[u].desc.empty() ? -1 : (int32_t)desc.size();
+    desc.insert(desc.end(), all[u].desc.begin(), all[u].desc.end());
     const size_t elems = (size_t)2 * (k > 1 ? k - 1 : 0) * k + 2 * (size_t)k;
     // complex: one longlong2 per entry; real: two int64 per longlong2
     toff += p->type == PERM_F64 ? (elems + 1) / 2 : elems;
   }
   p->table_elems = toff;
-  // slots: lane-mode matrices one slot, warp-mode one per item
+  p->nunits = nu;
+  // slots: lane-mode units one slot, warp-mode one per item
   int slot = 0;
-  struct Cost {
-    double cost;
-    int idx;
+  auto add_slot = [&](int u) {
+    slot_w.push_back(all[u].w);
+    return slot++;
   };
-  std::vector<Cost> order;
-  for (int k = 1; k <= kBatchKMax; ++k) {
-    std::vector<int> ms;
-    for (int m = 0; m < p->count; ++m)
-      if (p->ks[m] == k) ms.push_back(m);
-    if (ms.empty()) continue;
+  for (int u0 = 0; u0 < nu;) {
+    const int k = p->ks[all[u0].m], g = all[u0].g;
+    int u1 = u0;
+    while (u1 < nu && p->ks[all[u1].m] == k && all[u1].g == g) ++u1;
     if (p->cls_mode[k] == kLaneMode) {
-      for (size_t g = 0; g < ms.size(); g += 32) {
+      for (int q0 = u0; q0 < u1; q0 += 32) {
         BatchItem it;
         memset(&it, 0, sizeof(it));
         it.mode = kLaneMode;
         it.k = k;
-        it.c = k - 1;
-        it.count = (int)std::min<size_t>(32, ms.size() - g);
+        it.c = g;
+        it.count = std::min(32, u1 - q0);
         it.mat = (int)lane_mats.size();
         for (int q = 0; q < it.count; ++q) {
-          const int m = ms[g + q];
-          lane_mats.push_back(m);
-          mats[m].slot0 = slot++;
-          nslots[m] = 1;
+          lane_mats.push_back(q0 + q);
+          mats[q0 + q].slot0 = add_slot(q0 + q);
         }
         items.push_back(it);
       }
     } else {
-      const int c = p->cls_c[k];
-      const uint64_t nchunks = 1ull << (k - 1 - c);
+      const int c = std::min(p->cls_c[k], g);
+      const uint64_t nchunks = 1ull << (g - c);
       // complex k >= 16: lane pairs, 16 chunks per warp item
       const uint64_t per_item = (p->type == PERM_C128 && k >= 16) ? 16 : 32;
-      for (int m : ms) {
-        mats[m].slot0 = slot;
+      for (int u = u0; u < u1; ++u) {
+        mats[u].slot0 = slot;
         for (uint64_t ch = 0; ch < nchunks; ch += per_item) {
           BatchItem it;
           memset(&it, 0, sizeof(it));
@@ -616,20 +859,36 @@ static int batch_build(perm_batch_plan* p) {
           it.k = k;
           it.c = c;
           it.count = (int)per_item;
-          it.mat = m;
-          it.slot = slot++;
+          it.mat = u;
+          it.slot = add_slot(u);
           it.chunk0 = (int64_t)ch;
           items.push_back(it);
-          nslots[m]++;
         }
       }
     }
+    u0 = u1;
+  }
+  // output records: first unit, unit count and slot range of every matrix
+  for (int m = 0; m < p->count; ++m) outs[m] = {p->ks[m], -1, 0, 0, 0, 0};
+  for (int u = 0; u < nu; ++u) {
+    BatchOut& o = outs[all[u].m];
+    if (o.u0 < 0) {
+      o.u0 = u;
+      o.slot0 = mats[u].slot0;
+    }
+    o.nu++;
+  }
+  for (int m = 0; m < p->count; ++m) {
+    const BatchOut& o = outs[m];
+    const int ulast = o.u0 + o.nu - 1;
+    int end = ulast + 1 < nu ? mats[ulast + 1].slot0 : slot;
+    outs[m].nslots = end - o.slot0;
   }
   // longest first: cost ~ steps x k per item
   std::vector<size_t> idx(items.size());
   for (size_t i = 0; i < idx.size(); ++i) idx[i] = i;
   auto cost = [&](const BatchItem& it) {
-    double steps = it.mode == kLaneMode ? (double)(1ull << (it.k - 1)) : (double)(1ull << it.c);
+    double steps = (double)(1ull << it.c);
     return steps * (it.k + 4);
   };
   std::stable_sort(idx.begin(), idx.end(), [&](size_t x, size_t y) { return cost(items[x]) > cost(items[y]); });
@@ -641,19 +900,25 @@ static int batch_build(perm_batch_plan* p) {
   cudaFree(p->d_mats);
   cudaFree(p->d_items);
   cudaFree(p->d_lane_mats);
-  cudaFree(p->d_nslots);
+  cudaFree(p->d_outs);
+  cudaFree(p->d_desc);
+  cudaFree(p->d_slot_w);
   cudaFree(p->d_table);
   cudaFree(p->d_slots);
   p->d_mats = nullptr;
   p->d_items = nullptr;
   p->d_lane_mats = nullptr;
-  p->d_nslots = nullptr;
+  p->d_outs = nullptr;
+  p->d_desc = nullptr;
+  p->d_slot_w = nullptr;
   p->d_table = nullptr;
   p->d_slots = nullptr;
-  if (cudaMalloc(&p->d_mats, sizeof(BatchMat) * std::max(1, p->count)) != cudaSuccess ||
+  if (cudaMalloc(&p->d_mats, sizeof(BatchMat) * std::max(1, nu)) != cudaSuccess ||
       cudaMalloc(&p->d_items, sizeof(BatchItem) * std::max(1, p->nitems)) != cudaSuccess ||
       cudaMalloc(&p->d_lane_mats, sizeof(int32_t) * std::max<size_t>(1, lane_mats.size())) != cudaSuccess ||
-      cudaMalloc(&p->d_nslots, sizeof(int32_t) * std::max(1, p->count)) != cudaSuccess ||
+      cudaMalloc(&p->d_outs, sizeof(BatchOut) * std::max(1, p->count)) != cudaSuccess ||
+      cudaMalloc(&p->d_desc, sizeof(int32_t) * std::max<size_t>(1, desc.size())) != cudaSuccess ||
+      cudaMalloc(&p->d_slot_w, sizeof(double) * std::max(1, p->nslots_total)) != cudaSuccess ||
       cudaMalloc(&p->d_table, sizeof(longlong2) * std::max<size_t>(1, p->table_elems)) != cudaSuccess ||
       cudaMalloc(&p->d_slots, sizeof(dd) * 2 * std::max(1, p->nslots_total)) != cudaSuccess) {
     cudaGetLastError();
@@ -663,12 +928,15 @@ static int batch_build(perm_batch_plan* p) {
     cudaGetLastError();
     return PERM_ENOMEM;
   }
-  if (cudaMemcpy(p->d_mats, mats.data(), sizeof(BatchMat) * p->count, cudaMemcpyHostToDevice) != cudaSuccess ||
+  if (cudaMemcpy(p->d_mats, mats.data(), sizeof(BatchMat) * nu, cudaMemcpyHostToDevice) != cudaSuccess ||
       (p->nitems && cudaMemcpy(p->d_items, sorted.data(), sizeof(BatchItem) * p->nitems, cudaMemcpyHostToDevice) !=
                         cudaSuccess) ||
       (!lane_mats.empty() && cudaMemcpy(p->d_lane_mats, lane_mats.data(), sizeof(int32_t) * lane_mats.size(),
                                         cudaMemcpyHostToDevice) != cudaSuccess) ||
-      cudaMemcpy(p->d_nslots, nslots.data(), sizeof(int32_t) * p->count, cudaMemcpyHostToDevice) != cudaSuccess)
+      cudaMemcpy(p->d_outs, outs.data(), sizeof(BatchOut) * p->count, cudaMemcpyHostToDevice) != cudaSuccess ||
+      (!desc.empty() && cudaMemcpy(p->d_desc, desc.data(), sizeof(int32_t) * desc.size(), cudaMemcpyHostToDevice) !=
+                            cudaSuccess) ||
+      cudaMemcpy(p->d_slot_w, slot_w.data(), sizeof(double) * p->nslots_total, cudaMemcpyHostToDevice) != cudaSuccess)
     return PERM_ECUDA;
   return PERM_OK;
 }
@@ -678,6 +946,9 @@ static BatchArgs batch_args(const perm_batch_plan* p) {
   memset(&a, 0, sizeof(a));
   a.A = p->A;
   a.mats = p->d_mats;
+  a.outs = p->d_outs;
+  a.desc = p->d_desc;
+  a.slot_w = p->d_slot_w;
   a.items = p->d_items;
   a.lane_mats = p->d_lane_mats;
   a.table = p->d_table;
@@ -686,6 +957,7 @@ static BatchArgs batch_args(const perm_batch_plan* p) {
   a.out = p->out;
   a.status = p->status;
   a.nmats = p->count;
+  a.nunits = p->nunits;
   a.nitems = p->nitems;
   a.type = p->type;
   return a;
@@ -695,7 +967,7 @@ static BatchArgs batch_args(const perm_batch_plan* p) {
 static int batch_enqueue(const perm_batch_plan* p, cudaStream_t s) {
   BatchArgs a = batch_args(p);
   if (cudaMemsetAsync(p->d_counter, 0, sizeof(unsigned int), s) != cudaSuccess) return PERM_ECUDA;
-  batch_prep_kernel<<<p->count, kBlock, 0, s>>>(a);
+  batch_prep_kernel<<<p->nunits, kBlock, 0, s>>>(a);
   int nb = 0;
   const bool real = p->type == PERM_F64;
   const void* mk = real ? reinterpret_cast<const void*>(batch_main_kernel<true>)
@@ -707,7 +979,7 @@ static int batch_enqueue(const perm_batch_plan* p, cudaStream_t s) {
     batch_main_kernel<true><<<grid, kBlock, 0, s>>>(a);
   else
     batch_main_kernel<false><<<grid, kBlock, 0, s>>>(a);
-  batch_finish_kernel<<<(p->count + 127) / 128, 128, 0, s>>>(a, p->d_nslots);
+  batch_finish_kernel<<<(p->count + 127) / 128, 128, 0, s>>>(a);
   return cudaGetLastError() == cudaSuccess ? PERM_OK : PERM_ECUDA;
 }
 
@@ -730,9 +1002,8 @@ static int batch_capture(perm_batch_plan* p) {
   return rc;
 }
 
-extern "C" int perm_batched_plan_create(perm_batch_plan** plan, int type, const int* ns_host, int count,
-                                        const void* A_packed, const int64_t* offsets_host, void* out,
-                                        int32_t* status) {
+static int batch_create(perm_batch_plan** plan, int type, const int* ns_host, int count, const void* A_packed,
+                        const int64_t* offsets_host, void* out, int32_t* status, const int32_t* labels_host) {
   if (!plan) return PERM_EINVAL;
   *plan = nullptr;
   if (type != PERM_C128 && type != PERM_F64) return PERM_EINVAL;
@@ -759,6 +1030,14 @@ extern "C" int perm_batched_plan_create(perm_batch_plan** plan, int type, const 
       delete p;
       return PERM_EINVAL;
     }
+  if (labels_host) {
+    int64_t tot = 0;
+    for (int k : p->ks) {
+      p->lab_off.push_back(tot);
+      tot += k;
+    }
+    p->labels.assign(labels_host, labels_host + tot);
+  }
   p->A = static_cast<const double*>(A_packed);
   p->out = static_cast<double*>(out);
   p->status = status;
@@ -771,6 +1050,22 @@ extern "C" int perm_batched_plan_create(perm_batch_plan** plan, int type, const 
   }
   *plan = p;
   return PERM_OK;
+}
+
+extern "C" int perm_batched_plan_create(perm_batch_plan** plan, int type, const int* ns_host, int count,
+                                        const void* A_packed, const int64_t* offsets_host, void* out,
+                                        int32_t* status) {
+  return batch_create(plan, type, ns_host, count, A_packed, offsets_host, out, status, nullptr);
+}
+
+extern "C" int perm_batched_plan_create_labeled(perm_batch_plan** plan, int type, const int* ns_host, int count,
+                                                const void* A_packed, const int64_t* offsets_host, void* out,
+                                                int32_t* status, const int32_t* row_labels_host) {
+  if (!row_labels_host) {
+    if (plan) *plan = nullptr;
+    return PERM_EINVAL;
+  }
+  return batch_create(plan, type, ns_host, count, A_packed, offsets_host, out, status, row_labels_host);
 }
 
 extern "C" int perm_batched(perm_batch_plan* plan, void* stream) {
@@ -788,11 +1083,16 @@ extern "C" int perm_batched_autotune(perm_batch_plan* plan, int rounds, void* st
   int rc = PERM_OK;
   for (int k = 1; k <= kBatchKMax && !rc; ++k) {
     std::vector<int> ks;
-    std::vector<int64_t> offs;
+    std::vector<int64_t> offs, loffs;
+    std::vector<int32_t> labs;
     for (int m = 0; m < plan->count; ++m)
       if (plan->ks[m] == k) {
         ks.push_back(k);
         offs.push_back(plan->a_off[m]);
+        if (!plan->labels.empty()) {
+          loffs.push_back((int64_t)labs.size());
+          labs.insert(labs.end(), plan->labels.begin() + plan->lab_off[m], plan->labels.begin() + plan->lab_off[m] + k);
+        }
       }
     if (ks.empty()) continue;
     struct Cand {
@@ -812,6 +1112,8 @@ extern "C" int perm_batched_autotune(perm_batch_plan* plan, int rounds, void* st
       q->count = (int)ks.size();
       q->ks = ks;
       q->a_off = offs;
+      q->labels = labs;
+      q->lab_off = loffs;
       q->max_k = k;
       q->A = plan->A;
       q->out = plan->out;  // scratch use of the caller's output (rewritten below)

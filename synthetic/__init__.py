@@ -95,17 +95,20 @@ def complex_uniform(n: int, seed: int) -> np.ndarray:
     return (2.0 * g.random((n, n)) - 1.0) + 1j * (2.0 * g.random((n, n)) - 1.0)
 
 
-def boson_submatrices(count: int, seed: int, kmin: int = 8, kmax: int = 26, m: int = 256):
+def boson_submatrices(count: int, seed: int, kmin: int = 8, kmax: int = 26, m: int = 256,
+                      with_rows: bool = False):
     """k x k submatrices: k rows drawn with replacement from a Haar m x m unitary,
-    its first k columns; k uniform in [kmin, kmax]."""
+    its first k columns; k uniform in [kmin, kmax].  with_rows: also return the
+    drawn row (mode) indices of every matrix, which label its equal rows."""
     U = haar_unitary(m, seed)
     g = rng(seed + 1)
     ks = g.integers(kmin, kmax + 1, size=count)
-    out = []
+    out, idx = [], []
     for k in ks:
         rows = g.integers(0, m, size=int(k))
         out.append(np.ascontiguousarray(U[rows, : int(k)]))
-    return out
+        idx.append(rows.astype(np.int32))
+    return (out, idx) if with_rows else out
 
 
 # -------------------------------------------------------------------- sparse
@@ -220,8 +223,8 @@ def sparse_44():
     return sparse_real(44, SEED_BASE + 5, 0.2)
 
 
-def batched_boson(count: int = 8192):
-    return boson_submatrices(count, SEED_BASE + 6, 8, 26, 256)
+def batched_boson(count: int = 8192, with_rows: bool = False):
+    return boson_submatrices(count, SEED_BASE + 6, 8, 26, 256, with_rows)
 
 
 def grad_real_28():

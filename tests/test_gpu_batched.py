@@ -101,3 +101,77 @@ def test_real_plan_matches_single_matrix_kernel_and_autotune(pg):
         plan.run()
     assert plan.status.cpu().numpy().tolist() == [0, 1]
     plan.close()
+
+
+# ---------------------------------------------------- labelled (repeated) rows
+
+def test_labeled_boson_plan_vs_oracle(pg, oracle):
+    """Rows drawn with replacement from a small unitary (many repeats): the
+    multiplicity sweeps match the oracle and the unlabelled plan."""
+    mats, rows = syn.boson_submatrices(400, 21, 2, 16, 24, with_rows=True)
+    assert sum(len(set(r.tolist())) < len(r) for r in rows) > 150
+    plan = pg.BatchPlan(mats, row_labels=rows)
+    got = plan.run()
+    plain = pg.BatchPlan(mats).run()
+    for m, g, p in zip(mats, got, plain):
+        scale = max(1.0, oracle.perm_dp_f64(np.abs(m)))
+        assert abs(g - oracle.perm_dp_c128(m)) <= 1e-12 * scale
+        assert abs(g - p) <= 1e-12 * scale
+    assert np.array_equal(plan.run(), got)
+    plan.close()
+
+
+def test_labeled_chunked_sizes_and_autotune(pg):
+    """k = 17..24 with repeats: chunked sweeps on lane pairs with fewer Gray
+    bits than k - 1, before and after autotuning."""
+    import torch
+
+    mats, rows = syn.boson_submatrices(24, 22, 17, 24, 24, with_rows=True)
+    plan = pg.BatchPlan(mats, row_labels=rows)
+    got = plan.run()
+    for m, g in zip(mats, got):
+        single = pg.perm(torch.from_numpy(np.ascontiguousarray(m)).cuda())
+        assert abs(g - single) <= 1e-12 * max(1.0, abs(single))
+    plan.close()
+    plan = pg.BatchPlan(mats[:8], row_labels=rows[:8], autotune_rounds=1)
+    tuned = plan.run()
+    assert np.allclose(tuned, got[:8], rtol=1e-12, atol=1e-15)
+    plan.close()
+
+
+def test_labeled_real_plan_and_closed_forms(pg, oracle):
+    """float64 plans with repeated rows; k equal rows r give k! prod_j r_j."""
+    import math
+
+    g = syn.rng(23)
+    mats, labels = [], []
+    for k in [2, 3, 4, 6, 9, 12, 15, 16, 19] * 4:
+        lab = g.integers(0, max(2, k // 2), size=k).astype(np.int32)
+        B = 2.0 * g.random((k, k)) - 1.0
+        mats.append(B[lab])
+        labels.append(lab)
+    r = syn.signed_real(7, 2300)[0]
+    mats.append(np.tile(r, (7, 1)))
+    labels.append(np.full(7, 3, dtype=np.int32))
+    plan = pg.BatchPlan(mats, dtype="float64", row_labels=labels)
+    got = plan.run()
+    for m, v in zip(mats[:-1], got[:-1]):
+        assert abs(v - oracle.perm_dp_f64(m)) <= 1e-13 * oracle.perm_dp_f64(np.abs(m))
+    assert got[-1] == pytest.approx(math.factorial(7) * float(np.prod(r)), rel=1e-14)
+    plan.close()
+
+
+def test_labels_all_distinct_are_the_plain_plan_and_bad_labels_flagged(pg):
+    mats = syn.boson_submatrices(50, 24, 3, 14, 64)
+    labels = [np.arange(m.shape[0], dtype=np.int32) for m in mats]
+    assert np.array_equal(pg.BatchPlan(mats, row_labels=labels).run(), pg.BatchPlan(mats).run())
+    wrong = [l.copy() for l in labels]
+    wrong[7][1] = wrong[7][0]  # claims two different rows are equal
+    plan = pg.BatchPlan(mats, row_labels=wrong)
+    with pytest.raises(pg.PermError):
+        plan.run()
+    st = plan.status.cpu().numpy()
+    assert st[7] == 1 and (np.delete(st, 7) == 0).all()
+    plan.close()
+    with pytest.raises(ValueError):
+        pg.BatchPlan(mats[:2], row_labels=labels[:1])
