@@ -172,7 +172,10 @@ int perm_sparse(int n, const int32_t* cptrs, const int32_t* rids, const double* 
  *   in its status otherwise).  A matrix whose distinct rows occur mu_r times
  *   is then summed over the multiplicities (Glynn's form of Eq. 2 grouped by
  *   the number of copies of each row with sign -1, weights C(mu_r, k_r)),
- *   1/2 prod_r (mu_r + 1) terms instead of 2^(k-1); results agree with the
+ *   1/2 prod_r (mu_r + 1) terms instead of 2^(k-1) (at most 64 sweeps per
+ *   matrix, each of at least 2^min(k-1, 8) steps: further repeated rows are
+ *   swept as ordinary Gray bits, and a matrix where this does not pay keeps
+ *   the plain sweep, its labels still checked); results agree with the
  *   unlabelled plan to the accuracy of the kernels, not bitwise.
  *   row_labels_host NULL: PERM_EINVAL.
  * perm_batched - replay the plan's graph on stream (allocates nothing).

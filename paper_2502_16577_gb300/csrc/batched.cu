@@ -58,15 +58,18 @@ struct BatchMat {
   int32_t flags;  // 1: non-finite entry or unequal labelled rows, 2: zero row, 4: exponent range
   int32_t slot0;  // first partial slot of this unit
   int64_t a_off;  // element offset of the matrix in the packed input
-  int64_t d_off;  // longlong2 offset of its table (D, base, zero) in the plan
+  int64_t d_off;  // longlong2 offset of its column increments D (shared by a matrix's units)
+  int64_t b_off;  // longlong2 offset of its base and zero vectors
   int32_t g;      // Gray bits of the sweep: k - 1 for a plain matrix
   int32_t desc;   // -1: plain (rows of A are the factors); else the unit's descriptor
+  int32_t chk;    // -1, or the offset of P, (a, b) x P: labelled rows a, b that must be equal
 };
 
 // Descriptor of a transposed unit (ints, host-built): the fixed row f, the G
-// toggled rows, R (row, coefficient) pairs of the repeated rows, and P row
-// pairs that must be equal: f, G, t_0..t_{G-1}, R, (r, c) x R, P, (a, b) x P.
-// The factors are the columns of A.
+// toggled rows and R (row, coefficient) pairs of the repeated rows:
+// f, G, t_0..t_{G-1}, R, (r, c) x R.  The factors are the columns of A.  The
+// units of one matrix share D; the first of them (the one with the equality
+// checks, chk >= 0) writes it.
 
 // One output matrix: its units and its slots (contiguous).
 struct BatchOut {
@@ -105,6 +108,20 @@ struct BatchArgs {
   int type;               // PERM_C128 or PERM_F64
 };
 
+// Column i of the labelled row pairs at chk: 1 if some pair differs there.
+__device__ __forceinline__ int batch_labels_differ(const BatchArgs& a, const BatchMat& bm, int i) {
+  if (bm.chk < 0) return 0;
+  const int32_t* pp = a.desc + bm.chk;
+  const int P = pp[0];
+  const int w = a.type == PERM_F64 ? 1 : 2;
+  const double* col = a.A + (int64_t)w * (bm.a_off + i);
+  int bad = 0;
+  for (int t = 0; t < P; ++t)
+    for (int q = 0; q < w; ++q)
+      bad |= col[(int64_t)w * pp[1 + 2 * t] * bm.k + q] != col[(int64_t)w * pp[2 + 2 * t] * bm.k + q];
+  return bad;
+}
+
 // Transposed unit: factor i is column i of A; the toggles are rows, the
 // base holds the fixed row and the repeated rows times their coefficients.
 // Scales, rounding and the odd fixed row (real) follow the plain branch.
@@ -116,8 +133,6 @@ __device__ void batch_prep_transposed(const BatchArgs& a, const BatchMat& bm, in
   const int32_t* tg = d + 2;
   const int R = d[2 + G];
   const int32_t* rp = d + 3 + G;
-  const int P = rp[2 * R];
-  const int32_t* pp = rp + 2 * R + 1;
   const int i = threadIdx.x;
   if (i >= k) return;
   const bool real = a.type == PERM_F64;
@@ -131,23 +146,23 @@ __device__ void batch_prep_transposed(const BatchArgs& a, const BatchMat& bm, in
       fin &= isfinite(v) ? 1 : 0;
       absum += fabs(v);
     }
-  int bad = 0;
-  for (int t = 0; t < P; ++t)
-    for (int q = 0; q < w; ++q)
-      bad |= col[(int64_t)w * pp[2 * t] * k + q] != col[(int64_t)w * pp[2 * t + 1] * k + q];
+  const int bad = batch_labels_differ(a, bm, i);
   int kk = 0;
   if (fin && absum > 0.0) frexp(absum, &kk);
+  const bool wd = bm.chk >= 0;
   if (real) {
     long long* RD = reinterpret_cast<long long*>(a.table + bm.d_off);
-    long long* rbase = RD + (size_t)2 * (k > 1 ? k - 1 : 0) * k;
+    long long* rbase = reinterpret_cast<long long*>(a.table + bm.b_off);
     const int s = 61 - kk;
     auto q_of = [&](int r) { return fin ? __double2ll_rn(ldexp(col[(int64_t)r * k], s - 1)) : 0ll; };
     long long b = fin ? 2 * __double2ll_rd(ldexp(col[(int64_t)f * k], s - 1)) + 1 : 1;
     for (int j = 0; j < k - 1; ++j) {
       const long long q = j < G ? q_of(tg[j]) : 0;
       b -= 2 * q;
-      RD[(2 * j) * k + i] = 4 * q;
-      RD[(2 * j + 1) * k + i] = -4 * q;
+      if (wd) {
+        RD[(2 * j) * k + i] = 4 * q;
+        RD[(2 * j + 1) * k + i] = -4 * q;
+      }
     }
     for (int t = 0; t < R; ++t) b += (long long)rp[2 * t + 1] * 2 * q_of(rp[2 * t]);
     rbase[i] = b;
@@ -155,7 +170,7 @@ __device__ void batch_prep_transposed(const BatchArgs& a, const BatchMat& bm, in
     atomicAdd(&s_sum, s);
   } else {
     longlong2* D = a.table + bm.d_off;
-    longlong2* base = D + (size_t)2 * (k > 1 ? k - 1 : 0) * k;
+    longlong2* base = a.table + bm.b_off;
     const int s = 60 - kk;
     auto q_of = [&](int r, int part) {
       return fin ? __double2ll_rn(ldexp(col[(int64_t)2 * r * k + part], s)) : 0ll;
@@ -165,8 +180,10 @@ __device__ void batch_prep_transposed(const BatchArgs& a, const BatchMat& bm, in
       const long long qr = j < G ? q_of(tg[j], 0) : 0, qi = j < G ? q_of(tg[j], 1) : 0;
       br -= qr;
       bi -= qi;
-      D[(2 * j) * k + i] = make_longlong2(2 * qr, 2 * qi);
-      D[(2 * j + 1) * k + i] = make_longlong2(-2 * qr, -2 * qi);
+      if (wd) {
+        D[(2 * j) * k + i] = make_longlong2(2 * qr, 2 * qi);
+        D[(2 * j + 1) * k + i] = make_longlong2(-2 * qr, -2 * qi);
+      }
     }
     for (int t = 0; t < R; ++t) {
       br += (long long)rp[2 * t + 1] * q_of(rp[2 * t], 0);
@@ -188,7 +205,7 @@ __global__ void __launch_bounds__(kBlock) batch_prep_kernel(BatchArgs a) {
   const BatchMat bm = a.mats[m];
   const int k = bm.k;
   longlong2* D = a.table + bm.d_off;
-  longlong2* base = D + (size_t)2 * (k > 1 ? k - 1 : 0) * k;
+  longlong2* base = a.table + bm.b_off;
   longlong2* zero = base + k;
   __shared__ int s_sum, s_bound, s_flags;
   if (threadIdx.x == 0) {
@@ -203,7 +220,7 @@ __global__ void __launch_bounds__(kBlock) batch_prep_kernel(BatchArgs a) {
   } else if (a.type == PERM_F64) {
     // real: odd fixed-point rows as in real_stage (Y = 2 x 2^s)
     long long* RD = reinterpret_cast<long long*>(a.table + bm.d_off);
-    long long* rbase = RD + (size_t)2 * (k > 1 ? k - 1 : 0) * k;
+    long long* rbase = reinterpret_cast<long long*>(a.table + bm.b_off);
     long long* rzero = rbase + k;
     if (i < k) {
       const double* row = a.A + bm.a_off + (int64_t)i * k;
@@ -229,7 +246,7 @@ __global__ void __launch_bounds__(kBlock) batch_prep_kernel(BatchArgs a) {
       rzero[i] = 0;
       atomicAdd(&s_sum, s);
       atomicAdd(&s_bound, kk - 1);
-      if (!fin) atomicOr(&s_flags, 1);
+      if (!fin || batch_labels_differ(a, bm, i)) atomicOr(&s_flags, 1);
       if (fin && absum == 0.0) atomicOr(&s_flags, 2);
     }
   } else if (i < k) {
@@ -259,7 +276,7 @@ __global__ void __launch_bounds__(kBlock) batch_prep_kernel(BatchArgs a) {
     zero[i] = make_longlong2(0, 0);
     atomicAdd(&s_sum, s);
     atomicAdd(&s_bound, kk - 1);
-    if (!fin) atomicOr(&s_flags, 1);
+    if (!fin || batch_labels_differ(a, bm, i)) atomicOr(&s_flags, 1);
     if (fin && absum == 0.0) atomicOr(&s_flags, 2);
   }
   __syncthreads();
@@ -273,9 +290,8 @@ __global__ void __launch_bounds__(kBlock) batch_prep_kernel(BatchArgs a) {
 // Sweep steps t in [0, 2^c) of the chunk starting at g0 of a K x K matrix
 // whose table starts at D; adds the terms to (accr, acci).
 template <int K>
-__device__ __forceinline__ void batch_sweep(const longlong2* __restrict__ D, int sum_s, int c, uint64_t g0,
-                                            bool active, dd& accr, dd& acci) {
-  const longlong2* base = D + (size_t)2 * (K > 1 ? K - 1 : 0) * K;
+__device__ __forceinline__ void batch_sweep(const longlong2* __restrict__ D, const longlong2* __restrict__ base,
+                                            int sum_s, int c, uint64_t g0, bool active, dd& accr, dd& acci) {
   const longlong2* zero = base + K;
   const int ebase = 62 * (K + 1) - 120 - sum_s - K;
   const uint32_t nsteps = 1u << c;
@@ -339,9 +355,8 @@ __device__ __forceinline__ void batch_sweep(const longlong2* __restrict__ D, int
 // The real counterpart of batch_sweep: two integer product chains as in
 // ryser_real_kernel, the term split exactly into head and tail.
 template <int K>
-__device__ __forceinline__ void batch_sweep_real(const long long* __restrict__ D, int sum_s, int c, uint64_t g0,
-                                                 bool active, dd& acc) {
-  const long long* base = D + (size_t)2 * (K > 1 ? K - 1 : 0) * K;
+__device__ __forceinline__ void batch_sweep_real(const long long* __restrict__ D, const long long* __restrict__ base,
+                                                 int sum_s, int c, uint64_t g0, bool active, dd& acc) {
   const long long* zero = base + K;
   const int K1 = 64 * K + 1025 - sum_s;
   const uint32_t nsteps = 1u << c;
@@ -401,7 +416,8 @@ __device__ __forceinline__ void batch_item_real(const BatchArgs& a, const BatchI
     const BatchMat bm = a.mats[m];
     const bool ok = active && bm.flags == 0;
     if constexpr (K <= 16)  // one matrix per lane only for short sweeps (as complex)
-      batch_sweep_real<K>(reinterpret_cast<const long long*>(a.table + bm.d_off), bm.sum_s, bm.g, 0ull, ok, acc);
+      batch_sweep_real<K>(reinterpret_cast<const long long*>(a.table + bm.d_off),
+                          reinterpret_cast<const long long*>(a.table + bm.b_off), bm.sum_s, bm.g, 0ull, ok, acc);
     if (active) {
       a.slots[2 * bm.slot0] = acc;
       a.slots[2 * bm.slot0 + 1] = zero;
@@ -411,7 +427,8 @@ __device__ __forceinline__ void batch_item_real(const BatchArgs& a, const BatchI
     const uint64_t chunk = (uint64_t)it.chunk0 + lane;
     const uint64_t nchunks = 1ull << (bm.g - it.c);
     const bool active = chunk < nchunks && bm.flags == 0;
-    batch_sweep_real<K>(reinterpret_cast<const long long*>(a.table + bm.d_off), bm.sum_s, it.c,
+    batch_sweep_real<K>(reinterpret_cast<const long long*>(a.table + bm.d_off),
+                        reinterpret_cast<const long long*>(a.table + bm.b_off), bm.sum_s, it.c,
                         (active ? chunk : 0ull) << it.c, active, acc);
     acc = dd_warp_sum(acc);
     if (lane == 0) {
@@ -426,11 +443,10 @@ __device__ __forceinline__ void batch_item_real(const BatchArgs& a, const BatchI
 // one shuffle and one complex multiply combine the halves, each lane adds the
 // terms of every second step.
 template <int K>
-__device__ __forceinline__ void batch_sweep2(const longlong2* __restrict__ D, int sum_s, int c, uint64_t g0,
-                                             bool active, dd& accr, dd& acci) {
+__device__ __forceinline__ void batch_sweep2(const longlong2* __restrict__ D, const longlong2* __restrict__ base,
+                                             int sum_s, int c, uint64_t g0, bool active, dd& accr, dd& acci) {
   constexpr int R = (K + 1) / 2;
   const int li = threadIdx.x & 1;
-  const longlong2* base = D + (size_t)2 * (K - 1) * K;
   const int eoff = -(sum_s + K) - ((K & 1) ? 60 : 0);
   const uint32_t nsteps = 1u << c;
   const uint32_t kb = (uint32_t)((g0 >> c) & 1u) << c;
@@ -511,7 +527,7 @@ __device__ __forceinline__ void batch_item(const BatchArgs& a, const BatchItem& 
     const bool ok = active && bm.flags == 0;
     // one complex matrix per lane only for short sweeps (K <= 16, enforced by
     // the plan): longer rows would not fit the registers of a lane
-    if constexpr (K <= 16) batch_sweep<K>(a.table + bm.d_off, bm.sum_s, bm.g, 0ull, ok, accr, acci);
+    if constexpr (K <= 16) batch_sweep<K>(a.table + bm.d_off, a.table + bm.b_off, bm.sum_s, bm.g, 0ull, ok, accr, acci);
     if (active) {
       a.slots[2 * bm.slot0] = accr;
       a.slots[2 * bm.slot0 + 1] = acci;
@@ -522,10 +538,11 @@ __device__ __forceinline__ void batch_item(const BatchArgs& a, const BatchItem& 
     const uint64_t nchunks = 1ull << (bm.g - it.c);
     const bool active = chunk < nchunks && bm.flags == 0;
     if constexpr (K >= 16)
-      batch_sweep2<K>(a.table + bm.d_off, bm.sum_s, it.c, (active ? chunk : 0ull) << it.c, active, accr, acci);
+      batch_sweep2<K>(a.table + bm.d_off, a.table + bm.b_off, bm.sum_s, it.c, (active ? chunk : 0ull) << it.c, active,
+                      accr, acci);
     else
-      batch_sweep<(K < 16 ? K : 1)>(a.table + bm.d_off, bm.sum_s, it.c, (active ? chunk : 0ull) << it.c, active,
-                                    accr, acci);
+      batch_sweep<(K < 16 ? K : 1)>(a.table + bm.d_off, a.table + bm.b_off, bm.sum_s, it.c,
+                                    (active ? chunk : 0ull) << it.c, active, accr, acci);
     accr = dd_warp_sum(accr);
     acci = dd_warp_sum(acci);
     if (lane == 0) {
@@ -592,7 +609,7 @@ __global__ void batch_finish_kernel(BatchArgs a) {
     r = dd_add(r, w == 1.0 ? sr : dd_scale(sr, w));
     im = dd_add(im, w == 1.0 ? si : dd_scale(si, w));
   }
-  const BatchMat bm = {bo.k, 0, flags, 0, 0, 0, 0, 0};
+  const BatchMat bm = {bo.k, 0, flags, 0, 0, 0, 0, 0, 0, -1};
   const double f = (bm.k & 1) ? 2.0 : -2.0;
   const double nan = __longlong_as_double(0x7ff8000000000000ll);
   int32_t st = PERM_OK;
@@ -696,12 +713,13 @@ struct UnitPlan {
   int g;
   double w;
   std::vector<int32_t> desc;  // empty: plain
+  std::vector<int32_t> chk;   // empty, or P, (a, b) x P: labelled rows that must be equal
 };
 
 static void plan_units(const perm_batch_plan* p, int m, std::vector<UnitPlan>& units) {
   const int k = p->ks[m];
   units.clear();
-  UnitPlan plain{k - 1, 1.0, {}};
+  UnitPlan plain{k - 1, 1.0, {}, {}};
   if (p->labels.empty() || k < 2) {
     units.push_back(plain);
     return;
@@ -719,23 +737,42 @@ static void plan_units(const perm_batch_plan* p, int m, std::vector<UnitPlan>& u
     units.push_back(plain);
     return;
   }
+  std::vector<int32_t> chk(1, 0);
+  for (const auto& gr : groups)
+    for (size_t t = 1; t < gr.size(); ++t) {
+      chk.push_back(gr[0]);
+      chk.push_back(gr[t]);
+      chk[0]++;
+    }
+  plain.chk = chk;
   // fix one copy of a singleton row if there is one, else of the smallest group
   size_t fx = 0;
   for (size_t gi = 0; gi < groups.size(); ++gi)
     if (groups[gi].size() < groups[fx].size()) fx = gi;
   std::vector<int> tog;
   std::vector<std::pair<int, int>> repd;  // (row, multiplicity)
-  std::vector<std::pair<int, int>> pairs;
   for (size_t gi = 0; gi < groups.size(); ++gi) {
     const int mu = (int)groups[gi].size() - (gi == fx ? 1 : 0);
     const int r0 = groups[gi][0];
     if (mu == 1) tog.push_back(r0);
     else if (mu >= 2) repd.push_back({r0, mu});
-    for (size_t t = 1; t < groups[gi].size(); ++t) pairs.push_back({r0, groups[gi][t]});
   }
-  const int G = (int)tog.size();
+  // at most kMaxUnits combinations, each a sweep of at least 2^min(k-1, 8)
+  // steps: expand repeated groups back into Gray bits (smallest first: a
+  // pair costs 4/3 of its terms) until both hold
+  constexpr int kMaxUnits = 64;
+  const int gmin = std::min(k - 1, 8);
   double combos = 1.0;
   for (auto& rm : repd) combos *= rm.second + 1;
+  while ((combos > kMaxUnits || (int)tog.size() < gmin) && !repd.empty()) {
+    size_t sm = 0;
+    for (size_t t = 1; t < repd.size(); ++t)
+      if (repd[t].second < repd[sm].second) sm = t;
+    for (int q = 0; q < repd[sm].second; ++q) tog.push_back(repd[sm].first);
+    combos /= repd[sm].second + 1;
+    repd.erase(repd.begin() + sm);
+  }
+  const int G = (int)tog.size();
   if (std::ldexp(combos, G) >= std::ldexp(1.0, k - 1)) {
     units.push_back(plain);
     return;
@@ -760,12 +797,7 @@ static void plan_units(const perm_batch_plan* p, int m, std::vector<UnitPlan>& u
       for (int q = 0; q < kr[t]; ++q) c = c * (mu - q) / (q + 1);
       w *= (kr[t] & 1) ? -c : c;
     }
-    const size_t np = first ? pairs.size() : 0;  // equality checks once per matrix
-    u.desc.push_back((int32_t)np);
-    for (size_t t = 0; t < np; ++t) {
-      u.desc.push_back(pairs[t].first);
-      u.desc.push_back(pairs[t].second);
-    }
+    if (first) u.chk = chk;  // equality checks once per matrix
     u.w = w;
     units.push_back(std::move(u));
     size_t t = 0;
@@ -780,13 +812,14 @@ static int batch_build(perm_batch_plan* p) {
   struct Unit {
     int m, g, combo;
     double w;
-    std::vector<int32_t> desc;
+    std::vector<int32_t> desc, chk;
   };
   std::vector<Unit> all;
   std::vector<UnitPlan> ups;
   for (int m = 0; m < p->count; ++m) {
     plan_units(p, m, ups);
-    for (size_t c = 0; c < ups.size(); ++c) all.push_back({m, ups[c].g, (int)c, ups[c].w, std::move(ups[c].desc)});
+    for (size_t c = 0; c < ups.size(); ++c)
+      all.push_back({m, ups[c].g, (int)c, ups[c].w, std::move(ups[c].desc), std::move(ups[c].chk)});
   }
   // units of one size and Gray length together, then by matrix: the units
   // (and slots) of every matrix are contiguous
@@ -797,26 +830,45 @@ static int batch_build(perm_batch_plan* p) {
     return x.m < y.m;
   });
   const int nu = (int)all.size();
+  // D of every matrix (plain ones followed by their base and zero vectors),
+  // then base and zero of every transposed unit; in longlong2 units (a real
+  // table holds two int64 per longlong2)
+  const bool realt = p->type == PERM_F64;
+  auto d_size = [&](int k) -> int64_t { return (int64_t)(realt ? 1 : 2) * (k > 1 ? k - 1 : 0) * k; };
+  auto b_size = [&](int k) -> int64_t { return (int64_t)(realt ? 1 : 2) * k; };
+  std::vector<int64_t> dm(p->count);
+  std::vector<char> transposed(p->count, 0);
+  for (const Unit& un : all)
+    if (!un.desc.empty()) transposed[un.m] = 1;
+  size_t toff = 0;
+  for (int m = 0; m < p->count; ++m) {
+    dm[m] = (int64_t)toff;
+    toff += d_size(p->ks[m]) + (transposed[m] ? 0 : b_size(p->ks[m]));
+  }
   std::vector<BatchMat> mats(nu);
   std::vector<BatchOut> outs(p->count);
   std::vector<int32_t> desc;
   std::vector<double> slot_w;
   std::vector<BatchItem> items;
   std::vector<int32_t> lane_mats;
-  size_t toff = 0;
   for (int u = 0; u < nu; ++u) {
-    const int k = p->ks[all[u].m];
+    const int m = all[u].m, k = p->ks[m];
     mats[u].k = k;
     mats[u].sum_s = 0;
     mats[u].flags = 0;
-    mats[u].a_off = p->a_off[all[u].m];
-    mats[u].d_off = (int64_t)toff;
+    mats[u].a_off = p->a_off[m];
+    mats[u].d_off = dm[m];
+    if (transposed[m]) {
+      mats[u].b_off = (int64_t)toff;
+      toff += b_size(k);
+    } else {
+      mats[u].b_off = dm[m] + d_size(k);
+    }
     mats[u].g = all[u].g;
     mats[u].desc = all[u].desc.empty() ? -1 : (int32_t)desc.size();
     desc.insert(desc.end(), all[u].desc.begin(), all[u].desc.end());
-    const size_t elems = (size_t)2 * (k > 1 ? k - 1 : 0) * k + 2 * (size_t)k;
-    // complex: one longlong2 per entry; real: two int64 per longlong2
-    toff += p->type == PERM_F64 ? (elems + 1) / 2 : elems;
+    mats[u].chk = all[u].chk.empty() ? -1 : (int32_t)desc.size();
+    desc.insert(desc.end(), all[u].chk.begin(), all[u].chk.end());
   }
   p->table_elems = toff;
   p->nunits = nu;

@@ -175,3 +175,23 @@ def test_labels_all_distinct_are_the_plain_plan_and_bad_labels_flagged(pg):
     plan.close()
     with pytest.raises(ValueError):
         pg.BatchPlan(mats[:2], row_labels=labels[:1])
+
+
+def test_labeled_heavy_repeats_capped(pg):
+    """k = 12..24 rows drawn from 3..6 modes: thousands of multiplicity
+    combinations before the cap; the plan expands groups back into Gray bits
+    (at most 64 sweeps of at least 2^min(k-1, 8) steps per matrix)."""
+    import torch
+
+    mats, labels = [], []
+    for i, (k, modes) in enumerate([(12, 3), (16, 4), (18, 5), (20, 6), (22, 4), (24, 6), (13, 2), (9, 9)]):
+        U = syn.haar_unitary(max(modes, k), 2500 + i)
+        r = syn.rng(2600 + i).integers(0, modes, size=k).astype(np.int32)
+        mats.append(np.ascontiguousarray(U[r, :k]))
+        labels.append(r)
+    plan = pg.BatchPlan(mats, row_labels=labels)
+    got = plan.run()
+    for m, g in zip(mats, got):
+        single = pg.perm(torch.from_numpy(m).cuda())
+        assert abs(g - single) <= 1e-11 * max(1.0, abs(single))
+    plan.close()
