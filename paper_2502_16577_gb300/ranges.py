@@ -13,9 +13,9 @@ from __future__ import annotations
 
 import json
 
-from ._lib import PERM_BIN, PERM_C128, PERM_F64
+from ._lib import PERM_BIN, PERM_C128, PERM_F64, PERM_F64X
 
-WORDS = {PERM_F64: 2, PERM_C128: 4, PERM_BIN: 3}
+WORDS = {PERM_F64: 2, PERM_F64X: 2, PERM_C128: 4, PERM_BIN: 3}
 
 
 def total_steps(n: int) -> int:

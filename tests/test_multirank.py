@@ -26,12 +26,14 @@ def _free_port():
 
 def _oracle_partial(t, A, lo, hi):
     import oracle
-    from paper_2502_16577_gb300 import PERM_BIN, PERM_C128, PERM_F64
+    from paper_2502_16577_gb300 import PERM_BIN, PERM_C128, PERM_F64, PERM_F64X
 
     if lo == hi:
-        return 0 if t == PERM_BIN else (0.0,) * (2 if t == PERM_F64 else 4)
+        return 0 if t == PERM_BIN else (0.0,) * (2 if t in (PERM_F64, PERM_F64X) else 4)
     if t == PERM_F64:
         return oracle.ryser_f64_range(A, lo, hi, threads=2)
+    if t == PERM_F64X:  # extended products: the oracle's double-double range sum
+        return oracle.ryser_dd_range(A, lo, hi, threads=2)
     if t == PERM_C128:
         return oracle.ryser_c128_range(A, lo, hi, threads=2)
     v = oracle.ryser_bin_range(A, lo, hi, threads=2)  # residue mod 2^128 of a small sum
@@ -47,7 +49,7 @@ def _worker(rank, world, port, results, drop_rank):
         from paper_2502_16577_gb300 import ranges
 
         cases = [(pg.PERM_F64, syn.signed_real(13, 1)), (pg.PERM_C128, syn.haar_unitary(11, 2)),
-                 (pg.PERM_BIN, syn.bernoulli01(14, 3))]
+                 (pg.PERM_BIN, syn.bernoulli01(14, 3)), (pg.PERM_F64X, syn.signed_real(12, 4))]
         out = []
         for t, A in cases:
             n = A.shape[0]
@@ -89,8 +91,10 @@ def _port():
 
 
 def test_two_ranks_combine_to_the_full_permanent(oracle):
+    from fractions import Fraction
+
     res = _run(drop_rank=-1)
-    assert [r[0] for r in res] == ["ok", "ok", "ok"]
+    assert [r[0] for r in res] == ["ok", "ok", "ok", "ok"]
     want_r = oracle.perm_dp_f64(syn.signed_real(13, 1))
     want_c = oracle.perm_dp_c128(syn.haar_unitary(11, 2))
     want_b = oracle.perm_dp_bin(syn.bernoulli01(14, 3))
@@ -98,6 +102,10 @@ def test_two_ranks_combine_to_the_full_permanent(oracle):
     assert abs(res[0][1] - want_r) <= 1e-13 * scale
     assert abs(res[1][1] - want_c) <= 1e-13
     assert res[2][1] == want_b
+    hi, lo = res[3][1]
+    want_x = sum(map(Fraction, oracle.perm_dd(syn.signed_real(12, 4))))
+    assert abs(Fraction(hi) + Fraction(lo) - want_x) <= Fraction(1, 10 ** 27) * Fraction(
+        oracle.perm_dp_f64(np.abs(syn.signed_real(12, 4))))
 
 
 def test_a_rank_that_drops_its_range_is_detected(oracle):
