@@ -195,3 +195,29 @@ def test_labeled_heavy_repeats_capped(pg):
         single = pg.perm(torch.from_numpy(m).cuda())
         assert abs(g - single) <= 1e-11 * max(1.0, abs(single))
     plan.close()
+
+
+def test_labeled_edges_k1_k32_and_real_heavy(pg, oracle):
+    """k = 1 and 2 (nothing to group), k = 32 (the largest batched order, lane
+    pairs) drawn from 12 modes, and a real plan with rows from 3 modes."""
+    import torch
+
+    U = syn.haar_unitary(32, 2700)
+    r32 = syn.rng(2701).integers(0, 12, size=32).astype(np.int32)
+    mats = [U[:1, :1].copy(), U[[5, 5], :2].copy(), np.ascontiguousarray(U[r32, :32])]
+    labels = [np.array([0], np.int32), np.array([5, 5], np.int32), r32]
+    got = pg.BatchPlan(mats, row_labels=labels).run()
+    assert got[0] == mats[0][0, 0]
+    assert abs(got[1] - 2 * mats[1][0, 0] * mats[1][0, 1]) <= 1e-15
+    single = pg.perm(torch.from_numpy(mats[2]).cuda())
+    assert abs(got[2] - single) <= 1e-11 * max(1.0, abs(single))
+    g = syn.rng(2702)
+    reals, rl = [], []
+    for k in (10, 17, 23):
+        lab = g.integers(0, 3, size=k).astype(np.int32)
+        reals.append((2.0 * g.random((3, k)) - 1.0)[lab])
+        rl.append(lab)
+    gotr = pg.BatchPlan(reals, dtype="float64", row_labels=rl).run()
+    for m, v in zip(reals, gotr):
+        want = pg.perm(torch.from_numpy(np.ascontiguousarray(m)).cuda())
+        assert abs(v - want) <= 1e-12 * oracle.perm_dp_f64(np.abs(m))
