@@ -161,7 +161,8 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_secs / args.steps,
         "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": WORKLOAD, "oracle": "CPU Ryser/N-W (Alg. 1/3), pthreads"},
-        "cpu_baseline": {"value": value, "unit": "steps/s", "cores": threads, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "steps/s", "cores": threads, "kind": "oracle", "sample": sample,
+                         "host": host_cpu()},
         "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -188,6 +189,24 @@ def profiled_traffic(kernel_file: str, summary: str):
         if line.startswith("source_sha256_16:"):
             tag = line.split(":", 1)[1].strip()
     return traffic if tag == digest else None
+
+
+def host_cpu() -> str:
+    """The host CPU as the kernel reports it: machine, model name (x86) or
+    implementer / part (Arm), and the core count."""
+    import platform
+
+    model = ""
+    try:
+        info = open("/proc/cpuinfo").read().splitlines()
+        for key in ("model name", "CPU part"):
+            vals = [l.split(":", 1)[1].strip() for l in info if l.startswith(key)]
+            if vals:
+                model = f"{key} {vals[0]}"
+                break
+    except OSError:
+        pass
+    return f"{platform.machine()} {model} x{os.cpu_count() or 1}".strip()
 
 
 def measured_peaks():
@@ -356,7 +375,7 @@ def run_gpu(args):
         s, t = oracle_sample(8, os.cpu_count() or 1)
         line["cpu_baseline"] = {"value": s / t, "unit": "steps/s", "cores": os.cpu_count() or 1, "kind": "oracle",
                                 "sample": "first 2^-8 of each Gray range (real40 2^31, bin36 2^27, cplx32 2^23 steps)",
-                                "seconds": t}
+                                "seconds": t, "host": host_cpu()}
     print(json.dumps(line), flush=True)
     return 0
 
