@@ -88,9 +88,9 @@ typedef enum {
  * PERM_F64X uses the same fixed-point rows (column n-1 rounded to nearest,
  * so a row is exact when every a_ij 2^(60-k) is an integer, k the binary
  * exponent of the row's absolute sum) with 128-bit product mantissas
- * (2^-124 per factor), splits every term into a double-double without
+ * (2^-123 per factor), splits every term into a double-double without
  * losing more than 2^-105 of it, and renormalises the double-double after
- * every step; it costs about 3x PERM_F64.
+ * every step; it costs about 2.1x PERM_F64.
  * Binary matrices run in exact wrap-around integer arithmetic (192 bits).
  * Results are bitwise reproducible for a given n, type and GPU model.
  */

@@ -12,7 +12,7 @@
 //  * prod_i x_i carries a 128-bit mantissa (two 64-bit words) per chain.
 //    Each factor |Y_i| is first normalised to [2^63, 2^64), so one factor
 //    costs one 64 x 128 -> top-128-bit product and a shift of at most two
-//    bits; the relative error is below 2^-124 per factor (2^-61 in the
+//    bits; the relative error is below 2^-123 per factor (2^-61 in the
 //    default kernel).
 //  * Each term is split into a 53-bit head (truncated) and the rounded
 //    remainder, assembled from the mantissa with integer operations and one
@@ -44,20 +44,48 @@ __device__ __forceinline__ void shl128(unsigned long long& hi, unsigned long lon
   lo <<= s;
 }
 
-// p <- floor(M A / 2^64) up to the dropped low word of l*A, then shifted
-// left by s = clz - 1 so that M is back in [2^126, 2^127); returns s.
-// With M in [2^126, 2^127) and A in [2^63, 2^64) the unshifted value lies in
-// [2^125 - 1, 2^127), so s is 0, 1 or 2.
+// p <- floor(M A / 2^64) less under 3 units (dropped: l0 a0 and the low
+// words of l1 a0 and l0 a1), then shifted left by s so that M is back in
+// [2^126, 2^127); returns s.  With M in [2^126, 2^127) and A in [2^63, 2^64)
+// the unshifted value lies in [2^125 - 3, 2^127), so s is 0, 1 or 2 (31 for
+// a zero product).  PTX over 32-bit limbs: seven multiply-adds in one carry
+// chain, column by column, and a funnel-shift renormalisation.
 __device__ __forceinline__ uint32_t xprod_mul(XProd& p, unsigned long long A) {
-  const unsigned long long ph = __umul64hi(p.h, A);
-  const unsigned long long pl = p.h * A;
-  const unsigned long long c = __umul64hi(p.l, A);
-  unsigned long long lo = pl + c;
-  unsigned long long hi = ph + (lo < pl ? 1ull : 0ull);
-  const uint32_t s = (uint32_t)__clzll((long long)hi) - 1u;
-  shl128(hi, lo, s);
-  p.h = hi;
-  p.l = lo;
+  uint32_t s;
+  asm("{\n\t"
+      ".reg .u32 h0, h1, l0, l1, a0, a1, r0, r1, r2, r3, t;\n\t"
+      "mov.b64 {h0, h1}, %1;\n\t"
+      "mov.b64 {l0, l1}, %2;\n\t"
+      "mov.b64 {a0, a1}, %3;\n\t"
+      "mul.hi.u32 r0, l1, a0;\n\t"
+      "mul.hi.u32 t, l0, a1;\n\t"
+      "add.cc.u32 r0, r0, t;\n\t"
+      "addc.u32 r1, 0, 0;\n\t"
+      "mad.lo.cc.u32 r0, l1, a1, r0;\n\t"
+      "madc.hi.cc.u32 r1, l1, a1, r1;\n\t"
+      "addc.u32 r2, 0, 0;\n\t"
+      "mad.lo.cc.u32 r0, h0, a0, r0;\n\t"
+      "madc.hi.cc.u32 r1, h0, a0, r1;\n\t"
+      "addc.u32 r2, r2, 0;\n\t"
+      "mad.lo.cc.u32 r1, h0, a1, r1;\n\t"
+      "madc.hi.cc.u32 r2, h0, a1, r2;\n\t"
+      "addc.u32 r3, 0, 0;\n\t"
+      "mad.lo.cc.u32 r1, h1, a0, r1;\n\t"
+      "madc.hi.cc.u32 r2, h1, a0, r2;\n\t"
+      "addc.u32 r3, r3, 0;\n\t"
+      "mad.lo.cc.u32 r2, h1, a1, r2;\n\t"
+      "madc.hi.u32 r3, h1, a1, r3;\n\t"
+      "bfind.u32 t, r3;\n\t"
+      "sub.u32 %0, 30, t;\n\t"
+      "shf.l.wrap.b32 r3, r2, r3, %0;\n\t"
+      "shf.l.wrap.b32 r2, r1, r2, %0;\n\t"
+      "shf.l.wrap.b32 r1, r0, r1, %0;\n\t"
+      "shl.b32 r0, r0, %0;\n\t"
+      "mov.b64 %1, {r2, r3};\n\t"
+      "mov.b64 %2, {r0, r1};\n\t"
+      "}"
+      : "=r"(s), "+l"(p.h), "+l"(p.l)
+      : "l"(A));
   return s;
 }
 

@@ -4,7 +4,7 @@ GPU against exact and double-double references.
 The bound every test derives: the rows are exact on the inputs used here
 (every entry is a multiple of 2^-53 or a 0/1 value, and the row scale puts
 the row's absolute sum below 2^61), each of the n factors and the chain merge
-loses at most 2^-124 of the term, the head/tail split at most 2^-105, and the
+loses at most 2^-123 of the term, the head/tail split at most 2^-105, and the
 per-step renormalised double-double about 2^-104 of its running value.  So
 the unscaled sum is within 2^-95 S of the exact one, with S = sum_g |term_g|
 (2^-95 keeps a factor of 2^9 for the accumulation over a lane's steps), and
