@@ -178,6 +178,17 @@ int perm_sparse(int n, const int32_t* cptrs, const int32_t* rids, const double* 
  *   the plain sweep, its labels still checked); results agree with the
  *   unlabelled plan to the accuracy of the kernels, not bitwise.
  *   row_labels_host NULL: PERM_EINVAL.
+ * perm_batched_units - host only (no device call): the sweep units that a
+ *   labelled plan builds for one k x k matrix with row labels `labels`
+ *   (host int32[k], or NULL for all rows distinct).  Returns the number of
+ *   units (only the first max_units are written) or -status.  For unit u:
+ *   gray_bits[u] (its sweep has 2^gray_bits steps), weight[u] (its partial
+ *   sum is multiplied by weight[u] before the factor 2 (-1)^(k-1)), and
+ *   desc_off[u]: -1 for the plain sweep of A, else the offset in desc
+ *   (host int32[desc_cap]) of f, G, t_0..t_{G-1}, R, (r, c) x R: the sweep of
+ *   the transposed matrix with base row f, toggled rows t_j, and rows r added
+ *   c times to every column sum (x_j = (a_fj + sum_r c a_rj + sum_t d_t a_tj) / 2,
+ *   d_t = -1 at step 0).  -PERM_ENOMEM if desc_cap is too small.
  * perm_batched - replay the plan's graph on stream (allocates nothing).
  * perm_batched_autotune - time the candidate chunk exponents and the
  *   one-matrix-per-lane mode of every size class on the plan's own matrices
@@ -193,6 +204,8 @@ int perm_batched_plan_create(perm_batch_plan** plan, int type, const int* ns_hos
 int perm_batched_plan_create_labeled(perm_batch_plan** plan, int type, const int* ns_host, int count,
                                      const void* A_packed, const int64_t* offsets_host, void* out, int32_t* status,
                                      const int32_t* row_labels_host);
+int perm_batched_units(int k, const int32_t* labels, int max_units, int32_t* gray_bits, double* weight,
+                       int32_t* desc, int desc_cap, int32_t* desc_off);
 int perm_batched(perm_batch_plan* plan, void* stream);
 int perm_batched_autotune(perm_batch_plan* plan, int rounds, void* stream);
 int perm_batched_plan_info(const perm_batch_plan* plan, int k, int* mode, int* c, int* nitems);

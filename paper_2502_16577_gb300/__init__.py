@@ -21,7 +21,7 @@ import numpy as np
 from . import _lib
 from ._lib import PERM_BIN, PERM_C128, PERM_EABORTED, PERM_F64, PERM_F64X, PermError, check, load
 
-__all__ = ["perm", "perm_async", "perm_range", "perm_range_async", "perm_combine", "perm_sparse", "perm_sparse_async", "perm_host", "pipe_peaks", "BatchPlan", "AbortWord", "perm_grad", "perm_grad_async", "perm_grad_batched", "perm_grad_batched_async", "perm_grad_mixed", "permanent", "perm_type_of", "PermError",
+__all__ = ["perm", "perm_async", "perm_range", "perm_range_async", "perm_combine", "perm_sparse", "perm_sparse_async", "perm_host", "pipe_peaks", "BatchPlan", "AbortWord", "perm_grad", "perm_grad_async", "perm_grad_batched", "perm_grad_batched_async", "perm_grad_mixed", "permanent", "batched_units", "perm_type_of", "PermError",
            "PERM_F64", "PERM_C128", "PERM_BIN", "PERM_F64X", "perm_x", "PERM_EABORTED", "load"]
 
 
@@ -392,6 +392,41 @@ class AbortWord:
         if self._p:
             load().perm_abort_word_free(self._p)
             self._p = ctypes.POINTER(ctypes.c_uint32)()
+
+
+def batched_units(k: int, labels=None):
+    """The sweep units a labelled batched plan builds for one k x k matrix
+    (host only, perm_batched_units): a list of dicts with gray_bits, weight
+    and, for a sweep of the transposed matrix, fixed (row), toggles (rows)
+    and repeated ((row, coefficient) pairs); plain sweeps have fixed None."""
+    lib = load()
+    lab = None if labels is None else np.ascontiguousarray(np.asarray(labels, dtype=np.int32))
+    lp = ctypes.c_void_p(0) if lab is None else lab.ctypes.data_as(ctypes.c_void_p)
+    cnt = lib.perm_batched_units(int(k), lp, 0, None, None, None, 0, None)
+    if cnt < 0:
+        check(-cnt, "perm_batched_units")
+    g = np.zeros(cnt, dtype=np.int32)
+    w = np.zeros(cnt, dtype=np.float64)
+    off = np.zeros(cnt, dtype=np.int32)
+    cap = cnt * (2 * k + 4)
+    desc = np.zeros(max(cap, 1), dtype=np.int32)
+    rc = lib.perm_batched_units(int(k), lp, cnt, g.ctypes.data_as(ctypes.c_void_p), w.ctypes.data_as(ctypes.c_void_p),
+                                desc.ctypes.data_as(ctypes.c_void_p), cap, off.ctypes.data_as(ctypes.c_void_p))
+    if rc < 0:
+        check(-rc, "perm_batched_units")
+    out = []
+    for u in range(cnt):
+        d = {"gray_bits": int(g[u]), "weight": float(w[u]), "fixed": None, "toggles": [], "repeated": []}
+        if off[u] >= 0:
+            o = int(off[u])
+            d["fixed"] = int(desc[o])
+            G = int(desc[o + 1])
+            d["toggles"] = [int(x) for x in desc[o + 2:o + 2 + G]]
+            R = int(desc[o + 2 + G])
+            rp = desc[o + 3 + G:o + 3 + G + 2 * R]
+            d["repeated"] = [(int(rp[2 * t]), int(rp[2 * t + 1])) for t in range(R)]
+        out.append(d)
+    return out
 
 
 class BatchPlan:

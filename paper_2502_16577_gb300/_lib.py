@@ -18,7 +18,7 @@ _i32p = ctypes.POINTER(ctypes.c_int32)
 _lib = None
 
 SYMBOLS = ("perm", "perm_range", "perm_combine", "perm_sparse", "perm_host", "perm_pipe_peaks",
-           "perm_batched_plan_create", "perm_batched_plan_create_labeled", "perm_batched", "perm_batched_autotune", "perm_batched_plan_info",
+           "perm_batched_plan_create", "perm_batched_plan_create_labeled", "perm_batched_units", "perm_batched", "perm_batched_autotune", "perm_batched_plan_info",
            "perm_batched_plan_destroy", "perm_grad", "perm_grad_batched", "perm_grad_batched_mixed", "perm_decomp_create", "perm_decomp_info", "perm_decomp_leaf",
            "perm_decomp_filtered", "perm_decomp_eval", "perm_decomp_destroy", "perm_sparse_decomp",
            "perm_set_abort_word", "perm_abort_word_alloc", "perm_abort_word_free",
@@ -68,6 +68,8 @@ def load(build_if_missing: bool = False):
     lib.perm_batched_plan_create_labeled.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                                      ctypes.c_int, _vp, ctypes.POINTER(ctypes.c_int64), _vp, _vp,
                                                      ctypes.POINTER(ctypes.c_int32)]
+    lib.perm_batched_units.restype = ctypes.c_int
+    lib.perm_batched_units.argtypes = [ctypes.c_int, _vp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int, _vp]
     lib.perm_batched.restype = ctypes.c_int
     lib.perm_batched.argtypes = [_vp, _vp]
     lib.perm_batched_autotune.restype = ctypes.c_int

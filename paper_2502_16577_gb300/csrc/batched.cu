@@ -716,16 +716,15 @@ struct UnitPlan {
   std::vector<int32_t> chk;   // empty, or P, (a, b) x P: labelled rows that must be equal
 };
 
-static void plan_units(const perm_batch_plan* p, int m, std::vector<UnitPlan>& units) {
-  const int k = p->ks[m];
+static void plan_units_for(int k, const int32_t* labels, std::vector<UnitPlan>& units) {
   units.clear();
   UnitPlan plain{k - 1, 1.0, {}, {}};
-  if (p->labels.empty() || k < 2) {
+  if (!labels || k < 2) {
     units.push_back(plain);
     return;
   }
   // groups of equal labels, in order of first appearance
-  std::vector<int32_t> lab(p->labels.begin() + p->lab_off[m], p->labels.begin() + p->lab_off[m] + k);
+  std::vector<int32_t> lab(labels, labels + k);
   std::vector<std::vector<int>> groups;
   for (int r = 0; r < k; ++r) {
     size_t gi = 0;
@@ -804,6 +803,10 @@ static void plan_units(const perm_batch_plan* p, int m, std::vector<UnitPlan>& u
     while (t < repd.size() && ++kr[t] > repd[t].second) kr[t++] = 0;
     if (t == repd.size()) break;
   }
+}
+
+static void plan_units(const perm_batch_plan* p, int m, std::vector<UnitPlan>& units) {
+  plan_units_for(p->ks[m], p->labels.empty() ? nullptr : p->labels.data() + p->lab_off[m], units);
 }
 
 // Build the sweep units, work queue, slots and records for the current class
@@ -1118,6 +1121,26 @@ extern "C" int perm_batched_plan_create_labeled(perm_batch_plan** plan, int type
     return PERM_EINVAL;
   }
   return batch_create(plan, type, ns_host, count, A_packed, offsets_host, out, status, row_labels_host);
+}
+
+extern "C" int perm_batched_units(int k, const int32_t* labels, int max_units, int32_t* gray_bits, double* weight,
+                                  int32_t* desc, int desc_cap, int32_t* desc_off) {
+  if (k < 1 || k > kBatchKMax) return -PERM_ERANGE;
+  if (max_units < 0 || desc_cap < 0) return -PERM_EINVAL;
+  std::vector<UnitPlan> ups;
+  plan_units_for(k, labels, ups);
+  int pos = 0;
+  for (size_t u = 0; u < ups.size() && (int)u < max_units; ++u) {
+    if (gray_bits) gray_bits[u] = ups[u].g;
+    if (weight) weight[u] = ups[u].w;
+    if (desc_off) desc_off[u] = ups[u].desc.empty() ? -1 : pos;
+    if (!ups[u].desc.empty()) {
+      if (pos + (int)ups[u].desc.size() > desc_cap) return -PERM_ENOMEM;
+      if (desc) std::copy(ups[u].desc.begin(), ups[u].desc.end(), desc + pos);
+      pos += (int)ups[u].desc.size();
+    }
+  }
+  return (int)ups.size();
 }
 
 extern "C" int perm_batched(perm_batch_plan* plan, void* stream) {

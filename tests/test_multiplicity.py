@@ -102,3 +102,79 @@ def test_complex_rows_with_repeats(oracle):
         tr += w * pr
         ti += w * pi
     assert tr / 2 ** (n - 1) == re and ti / 2 ** (n - 1) == im
+
+
+# ------------------------------------------- the C++ planner, evaluated exactly
+
+def _perm_exact(A):
+    """Row-expansion subset DP over exact integers (the definition, Eq. 1)."""
+    n = len(A)
+    f = {0: 1}
+    for i in range(n):
+        g = {}
+        for S, v in f.items():
+            for j in range(n):
+                if not S >> j & 1 and A[i][j]:
+                    g[S | 1 << j] = g.get(S | 1 << j, 0) + v * A[i][j]
+        f = g
+    return f.get((1 << n) - 1, 0)
+
+
+def _eval_units(A, units):
+    """2 (-1)^(k-1) sum_u w_u sum_g (-1)^g prod_j x_j(g) in exact arithmetic."""
+    k = len(A)
+    total = Fraction(0)
+    for u in units:
+        G = u["gray_bits"]
+        s = Fraction(0)
+        for g in range(1 << G):
+            gr = g ^ (g >> 1)
+            prod = Fraction(1)
+            for j in range(k):
+                if u["fixed"] is None:  # plain sweep of A: rows are the factors
+                    x = A[j][k - 1] + sum(A[j][c] * (1 if gr >> c & 1 else -1) for c in range(k - 1))
+                else:  # transposed: columns are the factors
+                    x = A[u["fixed"]][j] + sum(c * A[r][j] for r, c in u["repeated"])
+                    x += sum(A[t][j] * (1 if gr >> b & 1 else -1) for b, t in enumerate(u["toggles"]))
+                prod *= Fraction(x, 2)
+            s += -prod if g & 1 else prod
+        total += Fraction(u["weight"]) * s
+    return 2 * (-1) ** (k - 1) * total
+
+
+@pytest.mark.parametrize("labels", [
+    [0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 3],      # one pair: 3 sweeps of 2^9 steps
+    [0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 5, 5],       # a triple
+    [0, 1, 2, 3, 4, 5, 6, 7, 8, 1, 2, 9, 3],    # three pairs
+    [0, 1, 0, 2, 1, 0, 2, 1, 0, 2, 1, 0],       # three modes: expanded back into Gray bits
+    [4] * 10,                                   # all rows equal: the plain sweep pays
+    list(range(9)),                             # all distinct: plain
+])
+def test_planned_units_sum_to_the_permanent(labels):
+    pg = pytest.importorskip("paper_2502_16577_gb300")
+    k = len(labels)
+    g = syn.rng(8300 + k)
+    B = g.integers(-3, 4, size=(max(labels) + 1, k))
+    A = [[int(v) for v in B[l]] for l in labels]
+    units = pg.batched_units(k, labels)
+    assert 1 <= len(units) <= 64
+    terms = sum(1 << u["gray_bits"] for u in units)
+    assert terms <= 1 << (k - 1)
+    if units[0]["fixed"] is not None:
+        assert terms < 1 << (k - 1)
+        assert all(u["gray_bits"] >= min(k - 1, 8) for u in units)
+    assert _eval_units(A, units) == _perm_exact(A)
+
+
+def test_planned_term_counts_on_the_boson_pattern():
+    """Rows drawn with replacement: one repeated pair among 26 rows gives three
+    sweeps of 2^23 steps (3/4 of 2^25); a triple gives four of 2^22."""
+    pg = pytest.importorskip("paper_2502_16577_gb300")
+    pair = list(range(25)) + [7]
+    u = pg.batched_units(26, pair)
+    assert [x["gray_bits"] for x in u] == [23] * 3
+    assert sorted(x["weight"] for x in u) == [-2.0, 1.0, 1.0]
+    triple = list(range(24)) + [7, 7]
+    u = pg.batched_units(26, triple)
+    assert [x["gray_bits"] for x in u] == [22] * 4
+    assert pg.batched_units(26, None)[0]["gray_bits"] == 25
