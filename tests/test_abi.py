@@ -63,6 +63,13 @@ def test_new_entry_points_check_arguments_on_the_host(lib):
     assert lib.perm_grad_batched(dummy, 4, -1, 0, dummy, dummy, vp(0), vp(0)) == 1
     # cancellation word: unregistering needs no device
     assert lib.perm_set_abort_word(None) == 0
+    # sweep-unit planner of labelled batched plans: host only
+    assert lib.perm_batched_units(0, None, 0, None, None, None, 0, None) == -2   # k < 1
+    assert lib.perm_batched_units(33, None, 0, None, None, None, 0, None) == -2  # k > 32
+    assert lib.perm_batched_units(5, None, 0, None, None, None, 0, None) == 1    # all distinct: one sweep
+    pair = (ctypes.c_int32 * 12)(*(list(range(11)) + [4]))
+    assert lib.perm_batched_units(12, pair, 0, None, None, None, 0, None) == 3
+    assert lib.perm_batched_units(12, pair, 3, None, None, None, 0, None) == -5  # no room for descriptors
 
 
 def test_host_argument_checks_need_no_gpu(lib):
