@@ -21,7 +21,7 @@ import numpy as np
 from . import _lib
 from ._lib import PERM_BIN, PERM_C128, PERM_EABORTED, PERM_F64, PERM_F64X, PermError, check, load
 
-__all__ = ["perm", "perm_async", "perm_range", "perm_range_async", "perm_combine", "perm_sparse", "perm_sparse_async", "perm_host", "pipe_peaks", "BatchPlan", "AbortWord", "perm_grad", "perm_grad_async", "perm_grad_batched", "perm_grad_batched_async", "perm_grad_mixed", "permanent", "batched_units", "perm_type_of", "PermError",
+__all__ = ["perm", "perm_async", "perm_range", "perm_range_async", "perm_combine", "perm_sparse", "perm_sparse_async", "perm_host", "pipe_peaks", "BatchPlan", "AbortWord", "perm_grad", "perm_grad_async", "perm_grad_batched", "perm_grad_batched_async", "perm_grad_mixed", "permanent", "batched_units", "equal_row_labels", "perm_type_of", "PermError",
            "PERM_F64", "PERM_C128", "PERM_BIN", "PERM_F64X", "perm_x", "PERM_EABORTED", "load"]
 
 
@@ -429,6 +429,13 @@ def batched_units(k: int, labels=None):
     return out
 
 
+def equal_row_labels(m) -> np.ndarray:
+    """Labels of the rows of one matrix: the index of the first bitwise-equal row."""
+    a = np.ascontiguousarray(m.detach().cpu().numpy() if hasattr(m, "detach") else np.asarray(m))
+    first = {}
+    return np.array([first.setdefault(a[i].tobytes(), i) for i in range(a.shape[0])], dtype=np.int32)
+
+
 class BatchPlan:
     """A batched plan over a list of square matrices (perm_batched_*), all
     complex128 or all float64 (dtype picks; default: complex128 unless every
@@ -440,7 +447,8 @@ class BatchPlan:
     row_labels (optional): one integer sequence per matrix, equal labels
     marking equal rows (e.g. the modes a boson-sampling submatrix was drawn
     from); such matrices are summed over row multiplicities, with fewer
-    terms.  Labelled rows are checked for equality on the device."""
+    terms.  Labelled rows are checked for equality on the device.  "auto"
+    labels the bitwise-equal rows of every matrix on the host."""
 
     def __init__(self, mats, device=None, autotune_rounds: int = 0, stream=None, dtype="complex128",
                  row_labels=None):
@@ -467,6 +475,10 @@ class BatchPlan:
         self._plan = ctypes.c_void_p(0)
         karr = (ctypes.c_int * len(ks))(*ks)
         oarr = (ctypes.c_int64 * len(ks))(*offs)
+        if isinstance(row_labels, str):
+            if row_labels != "auto":
+                raise ValueError('row_labels must be None, "auto" or one label sequence per matrix')
+            row_labels = [equal_row_labels(m) for m in mats]
         if row_labels is None:
             check(lib.perm_batched_plan_create(ctypes.byref(self._plan), self.type, karr, len(ks),
                                                ctypes.c_void_p(self.A.data_ptr()), oarr,

@@ -400,7 +400,8 @@ int perm_decomp_eval(perm_decomp* p, double* out, void* stream) {
   std::vector<int> bks, bidx(L, -1);
   size_t nd = 0, ncp = 0, nnz = 0, nb = 0;
   std::vector<double> hd, hv, hb;
-  std::vector<int32_t> hcp, hr;
+  std::vector<int32_t> hcp, hr, blab;  // blab: row labels of the batched leaves
+  bool repeats = false;
   for (size_t l = 0; l < L; ++l) {
     const Mat& m = d.leaves[l].m;
     if (m.n < 2) continue;
@@ -414,6 +415,15 @@ int perm_decomp_eval(perm_decomp* p, double* out, void* stream) {
       boff.push_back((int64_t)nb);
       hb.insert(hb.end(), m.a.begin(), m.a.end());
       nb += m.a.size();
+      // equal rows (bitwise) share a label, so the batched plan sums them
+      // over their multiplicities
+      for (int i = 0; i < m.n; ++i) {
+        int lab = i;
+        for (int r = 0; r < i && lab == i; ++r)
+          if (memcmp(&m.a[(size_t)r * m.n], &m.a[(size_t)i * m.n], sizeof(double) * m.n) == 0) lab = r;
+        repeats |= lab != i;
+        blab.push_back(lab);
+      }
     } else if (cnt * 10 >= (size_t)m.n * m.n * 3) {
       kind[l] = 2;
       off_dense[l] = nd;
@@ -466,7 +476,10 @@ int perm_decomp_eval(perm_decomp* p, double* out, void* stream) {
   cp(dd_bat, hb.data(), sizeof(double) * nb);
   perm_batch_plan* plan = nullptr;
   if (rc == PERM_OK && nbat) {
-    rc = perm_batched_plan_create(&plan, PERM_F64, bks.data(), (int)nbat, dd_bat, boff.data(), dd_bout, di_bst);
+    rc = repeats ? perm_batched_plan_create_labeled(&plan, PERM_F64, bks.data(), (int)nbat, dd_bat, boff.data(),
+                                                    dd_bout, di_bst, blab.data())
+                 : perm_batched_plan_create(&plan, PERM_F64, bks.data(), (int)nbat, dd_bat, boff.data(), dd_bout,
+                                            di_bst);
     if (rc == PERM_OK) rc = perm_batched(plan, stream);
   }
   for (size_t l = 0; l < L && rc == PERM_OK; ++l) {

@@ -221,3 +221,14 @@ def test_labeled_edges_k1_k32_and_real_heavy(pg, oracle):
     for m, v in zip(reals, gotr):
         want = pg.perm(torch.from_numpy(np.ascontiguousarray(m)).cuda())
         assert abs(v - want) <= 1e-12 * oracle.perm_dp_f64(np.abs(m))
+
+
+def test_auto_labels_match_the_drawn_modes(pg):
+    """row_labels="auto" finds the equal rows on the host: the same grouping
+    as the drawn modes, hence the same sweeps and the same bits."""
+    mats, rows = syn.boson_submatrices(200, 25, 8, 18, 32, with_rows=True)
+    by_mode = pg.BatchPlan(mats, row_labels=rows).run()
+    auto = pg.BatchPlan(mats, row_labels="auto").run()
+    assert np.array_equal(by_mode, auto)
+    with pytest.raises(ValueError):
+        pg.BatchPlan(mats[:2], row_labels="modes")

@@ -83,3 +83,21 @@ def test_structurally_singular_and_trivial(dec):
     assert dec.perm_sparse_decomp(Z)[0] == 0.0
     T = np.triu(0.5 + syn.rng(1501).random((40, 40)))
     assert dec.perm_sparse_decomp(T)[0] == pytest.approx(np.prod(np.diag(T)), rel=1e-14)
+
+
+def test_leaves_with_equal_rows_use_the_multiplicity_sweep(dec, oracle):
+    """Two dense 20 x 20 blocks whose rows repeat (12 distinct rows each),
+    shuffled: the Dulmage-Mendelsohn blocks are the leaves, and their equal
+    rows are labelled on the host, so the batched launch sums them over the
+    row multiplicities."""
+    g = syn.rng(1400)
+    blocks = []
+    for b in range(2):
+        rows = 1.0 - g.random((12, 20))
+        lab = np.concatenate([np.arange(12), g.integers(0, 12, size=8)])
+        blocks.append(rows[lab])
+    A = syn.shuffle_rows_cols(syn.block_diagonal(blocks), 1401)
+    got, info = dec.perm_sparse_decomp(A)
+    assert info["nblocks"] >= 2
+    want = oracle.perm_dp_f64(blocks[0]) * oracle.perm_dp_f64(blocks[1])
+    assert got == pytest.approx(want, rel=1e-10)

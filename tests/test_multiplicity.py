@@ -178,3 +178,13 @@ def test_planned_term_counts_on_the_boson_pattern():
     u = pg.batched_units(26, triple)
     assert [x["gray_bits"] for x in u] == [22] * 4
     assert pg.batched_units(26, None)[0]["gray_bits"] == 25
+
+
+def test_equal_row_labels_on_the_host():
+    pg = pytest.importorskip("paper_2502_16577_gb300")
+    m = np.array([[1.0, 2.0, 0.5], [3.0, 4.0, 0.5], [1.0, 2.0, 0.5]])
+    assert pg.equal_row_labels(m).tolist() == [0, 1, 0]
+    U = syn.haar_unitary(16, 8400)
+    r = [3, 7, 3, 3, 1, 7]
+    labels = pg.equal_row_labels(U[r, :6])
+    assert labels.tolist() == [0, 1, 0, 0, 4, 1]
