@@ -90,7 +90,8 @@ __device__ __forceinline__ uint32_t xprod_mul(XProd& p, unsigned long long A) {
 }
 
 // Merge two chains: M <- top 128 bits of Ma Mb / 2^128, renormalised; returns
-// the left shift (1..3: the unshifted value lies in [2^124 - 3, 2^126)).
+// the left shift (1..3: the unshifted value lies in [2^124 - 3, 2^126); 63
+// when a chain is zero).
 // Dropped: la*lb and the low words of the cross products (< 3 units).
 __device__ __forceinline__ uint32_t xprod_merge(XProd& a, const XProd& b) {
   const unsigned long long hh_hi = __umul64hi(a.h, b.h);
@@ -111,9 +112,9 @@ __device__ __forceinline__ uint32_t xprod_merge(XProd& a, const XProd& b) {
 // The term sign * M * 2^E as hi + lo, fb = E + 1149 the biased binary64
 // exponent of hi (M's top word lies in [2^62, 2^63), or M is zero).  hi
 // keeps the top 53 bits of M (truncated); lo is the remaining 74 bits,
-// rounded to 53 bits by
-// one conversion and moved to its exponent by an integer add.  Terms whose
-// head is below the normal range are flushed to zero; tails below it too.
+// rounded to 53 bits by one conversion and moved to its exponent by an
+// integer add.  Terms whose head is below the normal range are flushed to
+// zero; tails below it too.
 __device__ __forceinline__ void xprod_to_dd(const XProd& p, int fb, unsigned long long sign, double& hi,
                                             double& lo) {
   if (fb <= 0 || p.h == 0ull) {
