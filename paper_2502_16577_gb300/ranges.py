@@ -7,7 +7,10 @@ only exchange is the final sum of partials).
   (16-48 bytes) over an initialised torch.distributed group;
 * checkpoint / restore: completed ranges with their exact partials as JSON
   (binary64 words as hex), so a long sweep resumes where it stopped and the
-  combined result is bit-identical to an uninterrupted run.
+  combined result is bit-identical to an uninterrupted run;
+* shard_matrices / gather_results: a batch of independent permanents split
+  over ranks by matrix, longest first (cost 2^(k-1) k per k x k matrix, or
+  the caller's costs), and the per-rank results put back in batch order.
 """
 from __future__ import annotations
 
@@ -108,3 +111,50 @@ def gather_partials(dist, t: int, partial_words):
         else:
             out.append(tuple(p))
     return out
+
+
+def matrix_cost(k: int) -> float:
+    """Work of one k x k sweep: 2^(k-1) Gray steps of k factors each."""
+    return float(2 ** (k - 1) * k) if k > 0 else 0.0
+
+
+def shard_matrices(ks, world: int, costs=None):
+    """Indices of the matrices each of `world` ranks computes: longest
+    processing time first, each matrix to the least-loaded rank (ties to the
+    lower rank, so every rank derives the same assignment).  Returns a list of
+    `world` sorted index lists."""
+    if world < 1:
+        raise ValueError("bad world")
+    costs = [matrix_cost(int(k)) for k in ks] if costs is None else [float(c) for c in costs]
+    if len(costs) != len(ks):
+        raise ValueError("one cost per matrix")
+    load = [0.0] * world
+    parts = [[] for _ in range(world)]
+    for i in sorted(range(len(costs)), key=lambda i: (-costs[i], i)):
+        r = min(range(world), key=lambda q: (load[q], q))
+        parts[r].append(i)
+        load[r] += costs[i]
+    return [sorted(p) for p in parts]
+
+
+def gather_results(dist, indices, values, count: int):
+    """All-gather every rank's (index, value) results (complex or real) and
+    return the `count` values in batch order on every rank."""
+    import torch
+
+    vals = [complex(v) for v in values]
+    local = torch.tensor([[float(i), v.real, v.imag] for i, v in zip(indices, vals)], dtype=torch.float64).reshape(-1, 3)
+    sizes = [torch.zeros(1, dtype=torch.int64) for _ in range(dist.get_world_size())]
+    dist.all_gather(sizes, torch.tensor([local.shape[0]], dtype=torch.int64))
+    width = max(int(s.item()) for s in sizes)
+    padded = torch.zeros((width, 3), dtype=torch.float64)
+    padded[: local.shape[0]] = local
+    outs = [torch.zeros_like(padded) for _ in sizes]
+    dist.all_gather(outs, padded)
+    res = [None] * count
+    for o, sz in zip(outs, sizes):
+        for row in o[: int(sz.item())].tolist():
+            res[int(row[0])] = complex(row[1], row[2])
+    if any(v is None for v in res):
+        raise ValueError("some matrices were computed by no rank")
+    return res

@@ -152,3 +152,54 @@ def test_checkpoint_resume_is_bit_identical(oracle):
     bparts = [(a, b, (v - (1 << 128)) % (1 << 192) if v >= (1 << 127) else v) for a, b, v in bparts]
     t, nb, done = ranges.restore(ranges.checkpoint(pg.PERM_BIN, 12, bparts))
     assert pg.perm_combine(t, nb, [p for _, _, p in done]) == oracle.perm_dp_bin(B)
+
+
+# ------------------------------------------------- batches shard by matrix
+
+def test_batch_shards_cover_and_balance():
+    from paper_2502_16577_gb300 import ranges
+
+    g = syn.rng(77)
+    for world in (1, 2, 3, 8):
+        ks = [int(k) for k in g.integers(8, 27, size=500)]
+        parts = ranges.shard_matrices(ks, world)
+        assert sorted(i for p in parts for i in p) == list(range(len(ks)))
+        loads = [sum(ranges.matrix_cost(ks[i]) for i in p) for p in parts]
+        total, big = sum(loads), max(ranges.matrix_cost(k) for k in ks)
+        assert max(loads) <= total / world + big  # LPT: within one matrix of the mean
+        assert parts == ranges.shard_matrices(ks, world)  # every rank derives the same split
+    with pytest.raises(ValueError):
+        ranges.shard_matrices([3, 4], 2, costs=[1.0])
+
+
+def _batch_worker(rank, world, port, results):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import oracle
+        from paper_2502_16577_gb300 import ranges
+
+        mats = syn.boson_submatrices(30, 31, 3, 10, 32)
+        mine = ranges.shard_matrices([m.shape[0] for m in mats], world)[rank]
+        vals = [oracle.perm_dp_c128(mats[i]) for i in mine]  # stands in for this rank's batched plan
+        res = ranges.gather_results(dist, mine, vals, len(mats))
+        if rank == 0:
+            results.extend(res)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_ranks_share_a_batch(oracle):
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as m:
+        results = m.list()
+        procs = [ctx.Process(target=_batch_worker, args=(r, 2, _free_port_cache[0], results)) for r in range(2)]
+        for p in procs:
+            p.start()
+        for p in procs:
+            p.join(120)
+            assert p.exitcode == 0
+        got = list(results)
+    mats = syn.boson_submatrices(30, 31, 3, 10, 32)
+    assert got == [oracle.perm_dp_c128(x) for x in mats]
