@@ -32,6 +32,7 @@ def _torch():
 
 
 def perm_type_of(dtype) -> int:
+    """The perm_type_t of a torch dtype (float64, complex128, uint8/bool 0/1)."""
     torch = _torch()
     if dtype in (torch.float64,):
         return PERM_F64
@@ -499,6 +500,7 @@ class BatchPlan:
             check(lib.perm_batched_autotune(self._plan, int(autotune_rounds), h), "perm_batched_autotune")
 
     def run_async(self, stream=None) -> None:
+        """Replay the plan on a stream without waiting; results land in self.out."""
         h, _ = _stream_handle(stream)
         check(load().perm_batched(self._plan, h), "perm_batched")
 
@@ -515,6 +517,7 @@ class BatchPlan:
         return o.copy() if self.type == PERM_F64 else o[0::2] + 1j * o[1::2]
 
     def info(self, k: int):
+        """The size class choice for order k: mode, chunk exponent, queue length."""
         mode, c, n = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         check(load().perm_batched_plan_info(self._plan, int(k), ctypes.byref(mode), ctypes.byref(c), ctypes.byref(n)),
               "perm_batched_plan_info")

@@ -33,12 +33,15 @@ class DecompInfo(ctypes.Structure):
 
 
 class PermError(RuntimeError):
+    """A nonzero perm_status_t from the library; .code holds it."""
+
     def __init__(self, code: int, what: str = ""):
         self.code = int(code)
         super().__init__(f"{what}: {status_string(code)}" if what else status_string(code))
 
 
 def lib_path() -> str:
+    """Path of the in-tree libperm.so."""
     return _build.LIB
 
 
@@ -122,6 +125,7 @@ def load(build_if_missing: bool = False):
 
 
 def status_string(code: int) -> str:
+    """The library's text for a perm_status_t code."""
     try:
         return load().perm_status_string(int(code)).decode()
     except ImportError:
@@ -129,5 +133,6 @@ def status_string(code: int) -> str:
 
 
 def check(code: int, what: str = "") -> None:
+    """Raise PermError for a nonzero perm_status_t."""
     if int(code) != PERM_OK:
         raise PermError(code, what)

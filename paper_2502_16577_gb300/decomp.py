@@ -49,6 +49,7 @@ class SparseDecomposition:
         self._h = h
 
     def info(self) -> dict:
+        """Blocks, leaves and the Gray steps of the leaves against the plain sweep."""
         inf = DecompInfo()
         check(self._lib.perm_decomp_info(self._h, ctypes.byref(inf)), "perm_decomp_info")
         return {f: getattr(inf, f) for f, _ in DecompInfo._fields_}
@@ -74,6 +75,7 @@ class SparseDecomposition:
         return M
 
     def eval(self, stream=None) -> float:
+        """perm(A) from the leaves on the GPU, recombined on the host."""
         out = ctypes.c_double()
         h = ctypes.c_void_p(stream.cuda_stream) if stream is not None else ctypes.c_void_p(0)
         check(self._lib.perm_decomp_eval(self._h, ctypes.byref(out), h), "perm_decomp_eval")

@@ -22,6 +22,7 @@ WORDS = {PERM_F64: 2, PERM_F64X: 2, PERM_C128: 4, PERM_BIN: 3}
 
 
 def total_steps(n: int) -> int:
+    """Number of Gray steps of an n x n sweep, 2^(n-1) (0 for n = 0)."""
     return 1 << (n - 1) if n > 0 else 0
 
 
@@ -35,6 +36,7 @@ def shard(n_steps: int, rank: int, world: int):
 
 
 def split(n_steps: int, parts: int):
+    """The shards of all `parts` ranks, in rank order."""
     return [shard(n_steps, r, parts) for r in range(parts)]
 
 
@@ -58,6 +60,7 @@ def partial_to_words(t: int, value):
 
 
 def words_to_partial(t: int, words):
+    """Inverse of partial_to_words."""
     if t == PERM_BIN:
         return int(words[0], 16)
     return tuple(float.fromhex(w) for w in words)
@@ -70,6 +73,7 @@ def checkpoint(t: int, n: int, done) -> str:
 
 
 def restore(text: str):
+    """(type, n, done triples) from checkpoint() JSON."""
     d = json.loads(text)
     t = int(d["type"])
     return t, int(d["n"]), [(lo, hi, words_to_partial(t, w)) for lo, hi, w in d["done"]]
