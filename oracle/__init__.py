@@ -10,7 +10,8 @@ Two layers:
 * ``ryser.c`` (loaded through ctypes): Alg. 1 (RYSER in Nijenhuis-Wilf form,
   Eq. nwx) chunked over threads as in Alg. 3 (PARRYSER), for real FP64
   (double-double partial sums, Sec. 5), real with double-double x and products,
-  complex128, Alg. 2 (SPARYSER on CRS + CCS), exact 0/1 (Eq. 2 without halving
+  complex128, complex with x and products in double-double, rounding-error
+  magnitude sums (Sec. 5), Alg. 2 (SPARYSER on CRS + CCS), exact 0/1 (Eq. 2 without halving
   and Alg. 1 with doubled rows, both mod 2^128), and a row-by-row subset
   expansion of Eq. 1 that uses neither Ryser nor Gray codes.
 * pure Python, exact big integers / fractions: brute force over permutations
@@ -58,6 +59,10 @@ def load(mutant: int = 0):
     lib.oracle_cbl.restype = ctypes.c_int
     lib.oracle_cbl.argtypes = [ctypes.c_int, _ip]
     for name in ("oracle_ryser_f64_range", "oracle_ryser_dd_range", "oracle_ryser_c128_range"):
+        f = getattr(lib, name)
+        f.restype = ctypes.c_int
+        f.argtypes = [_dp, ctypes.c_int, _u64, _u64, ctypes.c_int, _dp]
+    for name in ("oracle_ryser_dd_stats_range", "oracle_ryser_cdd_range"):
         f = getattr(lib, name)
         f.restype = ctypes.c_int
         f.argtypes = [_dp, ctypes.c_int, _u64, _u64, ctypes.c_int, _dp]
@@ -171,6 +176,31 @@ def perm_dd(A, threads: int | None = None) -> tuple:
     rc = load().oracle_perm_dd(A.ctypes.data_as(_dp), A.shape[0], threads or default_threads(), out)
     _check(rc, "perm_dd")
     return out[0], out[1]
+
+
+def ryser_dd_stats_range(A, g0: int, g1: int, threads: int | None = None, mutant: int = 0) -> dict:
+    """The double-double range sum of ryser_dd_range plus two magnitude sums
+    (Sec. 5's error analysis): S = sum_g |prod_i x_i(g)| and
+    W = sum_g sum_i R_i prod_{k != i} |x_k(g)| with R_i = sum_j |a_ij|.
+    Returns {"hi", "lo", "S", "W"}."""
+    A = _real(A)
+    out = (ctypes.c_double * 4)()
+    rc = load(mutant).oracle_ryser_dd_stats_range(A.ctypes.data_as(_dp), A.shape[0], g0, g1,
+                                                  threads or default_threads(), out)
+    _check(rc, "ryser_dd_stats_range")
+    return {"hi": out[0], "lo": out[1], "S": out[2], "W": out[3]}
+
+
+def ryser_cdd_range(A, g0: int, g1: int, threads: int | None = None, mutant: int = 0) -> dict:
+    """Complex range sum with x and every product in double-double, plus S and W
+    as in ryser_dd_stats_range (moduli of complex values).  Returns
+    {"re_hi", "re_lo", "im_hi", "im_lo", "S", "W"}."""
+    A = _cplx(A)
+    out = (ctypes.c_double * 6)()
+    rc = load(mutant).oracle_ryser_cdd_range(A.view(np.float64).ctypes.data_as(_dp), A.shape[0], g0, g1,
+                                             threads or default_threads(), out)
+    _check(rc, "ryser_cdd_range")
+    return {"re_hi": out[0], "re_lo": out[1], "im_hi": out[2], "im_lo": out[3], "S": out[4], "W": out[5]}
 
 
 def ryser_c128_range(A, g0: int, g1: int, threads: int | None = None) -> complex:

@@ -22,6 +22,11 @@
  *                                      accuracy study.
  *   oracle_ryser_c128_range            Alg. 1 over complex entries (complex support is
  *                                      claimed in Secs. 1 and 7; same recurrence in C).
+ *   oracle_ryser_dd_stats_range,       Alg. 1 in double-double (real; complex with the
+ *   oracle_ryser_cdd_range             four-multiply product), also returning the
+ *                                      magnitude sums that scale the rounding errors
+ *                                      studied in Sec. 5 (sum of |terms|, and the same
+ *                                      with one factor replaced by its row's size).
  *   oracle_spa_ryser_f64_range         Alg. 2 (SPARYSER): CRS for the row sums, CCS for
  *                                      the column updates.
  *   oracle_ryser_bin_plain             Eq. 2 (Ryser over all 2^n column subsets, no
@@ -499,6 +504,238 @@ int oracle_perm_c128(const double* A, int n, int threads, double* out) {
   double f = 4.0 * (double)(n % 2) - 2.0;
   out[0] = (s[0] + s[1]) * f;
   out[1] = (s[2] + s[3]) * f;
+  return 0;
+}
+
+/* ------------------------ Alg. 1 in double-double, with rounding statistics */
+/*
+ * Sec. 5 relates the accuracy of the sweep to the size of its terms.  The two
+ * sweeps below run Alg. 1 with x and every product in double-double (real, and
+ * complex with the standard four-multiply product) and also return two sums
+ * of magnitudes that scale rounding errors:
+ *   S = sum_g |prod_i x_i(g)|                        (the size of every term)
+ *   W = sum_g sum_i R_i prod_{k != i} |x_k(g)|,  R_i = sum_j |a_ij|
+ * A relative error eps in every term moves the range sum by at most eps S; an
+ * error of at most eps R_i in each x_i(g) moves it by at most about eps W
+ * (first order).  |.| is the modulus for complex entries.  Both sums are
+ * formed in binary64 per step from the leading words and added up in
+ * double-double: they are magnitudes for error bounds, not exact values.
+ */
+
+typedef struct {
+  dd_t p, s, w;
+} dd_stats_t;
+
+/* S and W of one term from the moduli xa[i] = |x_i(g)| and R[i]. */
+static void stats_step(const double* xa, const double* R, int n, dd_stats_t* st) {
+  double pre[ORACLE_NMAX + 1];
+  pre[0] = 1.0;
+  for (int i = 0; i < n; ++i) pre[i + 1] = pre[i] * xa[i]; /* prod_{k < i} |x_k| */
+  double suf = 1.0, w = 0.0;                             /* suf = prod_{k > i} |x_k| */
+  for (int i = n - 1; i >= 0; --i) {
+#if ORACLE_MUTANT == 9
+    w += pre[i] * suf; /* planted: row weight R_i dropped */
+#else
+    w += R[i] * pre[i] * suf;
+#endif
+    suf *= xa[i];
+  }
+  st->s = dd_add_d(st->s, pre[n]);
+  st->w = dd_add_d(st->w, w);
+}
+
+static void ryser_dd_stats_body(const void* vctx, uint64_t s, uint64_t e, void* out) {
+  const real_ctx_t* c = (const real_ctx_t*)vctx;
+  const double* A = c->A;
+  int n = c->n;
+  dd_t x[ORACLE_NMAX];
+  double R[ORACLE_NMAX], xa[ORACLE_NMAX];
+  for (int i = 0; i < n; ++i) { /* Alg. 1 start state, in double-double */
+    dd_t sum = DD_ZERO;
+    double r = 0.0;
+    for (int j = 0; j < n; ++j) {
+      sum = dd_add_d(sum, A[i * n + j]);
+      r += fabs(A[i * n + j]);
+    }
+    dd_t half = {sum.hi / 2.0, sum.lo / 2.0};
+    x[i] = dd_add_d(dd_neg(half), A[i * n + (n - 1)]);
+    R[i] = r;
+  }
+  dd_stats_t st = {DD_ZERO, DD_ZERO, DD_ZERO};
+  uint64_t start = s;
+  if (s == 0) { /* the g = 0 term: product of the start state */
+    dd_t prod = {1.0, 0.0};
+    for (int i = 0; i < n; ++i) {
+      prod = dd_mul(prod, x[i]);
+      xa[i] = fabs(x[i].hi);
+    }
+    st.p = dd_add(st.p, prod);
+    stats_step(xa, R, n, &st);
+    start = 1;
+  }
+  if (start < e) { /* Alg. 3: x at Gray_{start-1} */
+    uint64_t G = oracle_gray(start - 1);
+    for (int j = 0; j < n - 1; ++j)
+      if ((G >> j) & 1u)
+        for (int i = 0; i < n; ++i) x[i] = dd_add_d(x[i], A[i * n + j]);
+  }
+  for (uint64_t g = start; g < e; ++g) {
+    int j = oracle_changed_bit(g);
+    double sg = 2.0 * (double)((oracle_gray(g) >> j) & 1u) - 1.0;
+    dd_t prod = {1.0, 0.0};
+    for (int i = 0; i < n; ++i) {
+      x[i] = dd_add_d(x[i], sg * A[i * n + j]);
+      prod = dd_mul(prod, x[i]);
+      xa[i] = fabs(x[i].hi);
+    }
+    st.p = (g & 1u) ? dd_add(st.p, dd_neg(prod)) : dd_add(st.p, prod);
+    stats_step(xa, R, n, &st);
+  }
+  *(dd_stats_t*)out = st;
+}
+
+/* out = {sum hi, sum lo, S, W} for the range [g0, g1); the sum is the one of
+ * oracle_ryser_dd_range (x and products in double-double). */
+int oracle_ryser_dd_stats_range(const double* A, int n, uint64_t g0, uint64_t g1, int threads, double* out) {
+  int rc = check_range(n, g0, g1);
+  if (rc) return rc;
+  real_ctx_t ctx = {A, n};
+  int tau = threads < 1 ? 1 : threads;
+  dd_stats_t* parts = (dd_stats_t*)calloc((size_t)tau, sizeof(dd_stats_t));
+  if (!parts) return -3;
+  if (run_chunks(&ctx, g0, g1, tau, ryser_dd_stats_body, parts, sizeof(dd_stats_t))) {
+    free(parts);
+    return -3;
+  }
+  dd_stats_t tot = {DD_ZERO, DD_ZERO, DD_ZERO};
+  for (int t = 0; t < tau; ++t) { /* outer sum, fixed order */
+    tot.p = dd_add(tot.p, parts[t].p);
+    tot.s = dd_add(tot.s, parts[t].s);
+    tot.w = dd_add(tot.w, parts[t].w);
+  }
+  free(parts);
+  out[0] = tot.p.hi;
+  out[1] = tot.p.lo;
+  out[2] = tot.s.hi + tot.s.lo;
+  out[3] = tot.w.hi + tot.w.lo;
+  return 0;
+}
+
+/* complex double-double: (a + ib)(c + id) = (ac - bd) + i(ad + bc) */
+typedef struct {
+  dd_t re, im;
+} cdd_val_t;
+
+static cdd_val_t cdd_mul(cdd_val_t a, cdd_val_t b) {
+  cdd_val_t r;
+  r.re = dd_add(dd_mul(a.re, b.re), dd_neg(dd_mul(a.im, b.im)));
+#if ORACLE_MUTANT == 8
+  r.im = dd_add(dd_mul(a.re, b.im), dd_neg(dd_mul(a.im, b.re))); /* planted: sign of a cross term */
+#else
+  r.im = dd_add(dd_mul(a.re, b.im), dd_mul(a.im, b.re));
+#endif
+  return r;
+}
+
+typedef struct {
+  dd_t pr, pi, s, w;
+} cdd_stats_t;
+
+static void ryser_cdd_body(const void* vctx, uint64_t s, uint64_t e, void* out) {
+  const cplx_ctx_t* c = (const cplx_ctx_t*)vctx;
+  const double* A = c->A; /* (re, im) pairs */
+  int n = c->n;
+  cdd_val_t x[ORACLE_NMAX];
+  double R[ORACLE_NMAX], xa[ORACLE_NMAX];
+  for (int i = 0; i < n; ++i) { /* x_i = a_{i,n} - (sum_j a_ij) / 2, both parts */
+    dd_t sr = DD_ZERO, si = DD_ZERO;
+    double r = 0.0;
+    for (int j = 0; j < n; ++j) {
+      sr = dd_add_d(sr, A[2 * (i * n + j)]);
+      si = dd_add_d(si, A[2 * (i * n + j) + 1]);
+      r += hypot(A[2 * (i * n + j)], A[2 * (i * n + j) + 1]);
+    }
+    dd_t half_re = {sr.hi / 2.0, sr.lo / 2.0}, half_im = {si.hi / 2.0, si.lo / 2.0};
+    x[i].re = dd_add_d(dd_neg(half_re), A[2 * (i * n + n - 1)]);
+    x[i].im = dd_add_d(dd_neg(half_im), A[2 * (i * n + n - 1) + 1]);
+    R[i] = r;
+  }
+  dd_stats_t st = {DD_ZERO, DD_ZERO, DD_ZERO};
+  dd_t pim = DD_ZERO;
+  uint64_t start = s;
+  if (s == 0) {
+    cdd_val_t prod = {{1.0, 0.0}, DD_ZERO};
+    for (int i = 0; i < n; ++i) {
+      prod = cdd_mul(prod, x[i]);
+      xa[i] = hypot(x[i].re.hi, x[i].im.hi);
+    }
+    st.p = dd_add(st.p, prod.re);
+    pim = dd_add(pim, prod.im);
+    stats_step(xa, R, n, &st);
+    start = 1;
+  }
+  if (start < e) {
+    uint64_t G = oracle_gray(start - 1);
+    for (int j = 0; j < n - 1; ++j)
+      if ((G >> j) & 1u)
+        for (int i = 0; i < n; ++i) {
+          x[i].re = dd_add_d(x[i].re, A[2 * (i * n + j)]);
+          x[i].im = dd_add_d(x[i].im, A[2 * (i * n + j) + 1]);
+        }
+  }
+  for (uint64_t g = start; g < e; ++g) {
+    int j = oracle_changed_bit(g);
+    double sg = 2.0 * (double)((oracle_gray(g) >> j) & 1u) - 1.0;
+    cdd_val_t prod = {{1.0, 0.0}, DD_ZERO};
+    for (int i = 0; i < n; ++i) {
+      x[i].re = dd_add_d(x[i].re, sg * A[2 * (i * n + j)]);
+      x[i].im = dd_add_d(x[i].im, sg * A[2 * (i * n + j) + 1]);
+      prod = cdd_mul(prod, x[i]);
+      xa[i] = hypot(x[i].re.hi, x[i].im.hi);
+    }
+    if (g & 1u) {
+      st.p = dd_add(st.p, dd_neg(prod.re));
+      pim = dd_add(pim, dd_neg(prod.im));
+    } else {
+      st.p = dd_add(st.p, prod.re);
+      pim = dd_add(pim, prod.im);
+    }
+    stats_step(xa, R, n, &st);
+  }
+  cdd_stats_t* o = (cdd_stats_t*)out;
+  o->pr = st.p;
+  o->pi = pim;
+  o->s = st.s;
+  o->w = st.w;
+}
+
+/* out = {re hi, re lo, im hi, im lo, S, W}: the complex range sum of Alg. 1
+ * with x and every product in double-double. */
+int oracle_ryser_cdd_range(const double* A, int n, uint64_t g0, uint64_t g1, int threads, double* out) {
+  int rc = check_range(n, g0, g1);
+  if (rc) return rc;
+  cplx_ctx_t ctx = {A, n};
+  int tau = threads < 1 ? 1 : threads;
+  cdd_stats_t* parts = (cdd_stats_t*)calloc((size_t)tau, sizeof(cdd_stats_t));
+  if (!parts) return -3;
+  if (run_chunks(&ctx, g0, g1, tau, ryser_cdd_body, parts, sizeof(cdd_stats_t))) {
+    free(parts);
+    return -3;
+  }
+  cdd_stats_t tot = {DD_ZERO, DD_ZERO, DD_ZERO, DD_ZERO};
+  for (int t = 0; t < tau; ++t) {
+    tot.pr = dd_add(tot.pr, parts[t].pr);
+    tot.pi = dd_add(tot.pi, parts[t].pi);
+    tot.s = dd_add(tot.s, parts[t].s);
+    tot.w = dd_add(tot.w, parts[t].w);
+  }
+  free(parts);
+  out[0] = tot.pr.hi;
+  out[1] = tot.pr.lo;
+  out[2] = tot.pi.hi;
+  out[3] = tot.pi.lo;
+  out[4] = tot.s.hi + tot.s.lo;
+  out[5] = tot.w.hi + tot.w.lo;
   return 0;
 }
 

@@ -318,3 +318,106 @@ def test_generators_are_deterministic():
     assert (S != 0).any(axis=0).all() and (S != 0).any(axis=1).all()
     assert ((S == 0) | ((S > 0) & (S <= 1))).all()
     assert np.all(syn.signed_real(40, 1) * 2 ** 52 == np.round(syn.signed_real(40, 1) * 2 ** 52))
+
+
+# --------------------------------------- double-double sweeps with magnitude sums
+
+def _stats_by_definition(A):
+    """S and W of the full range computed from scratch for every subset (no Gray
+    updates): x_i(T) = (1/2) sum_j d_j a_ij with d_j = +1 for j in T or j = n-1,
+    else -1 (Eq. nwx); S = sum_T |prod_i x_i|, W = sum_T sum_i R_i prod_{k != i} |x_k|,
+    R_i = sum_j |a_ij|.  Exact rational arithmetic for real entries."""
+    A = np.asarray(A)
+    n = A.shape[0]
+    cplx = np.iscomplexobj(A)
+    R = [math.fsum(abs(complex(v)) for v in A[i]) for i in range(n)]
+    S, W = 0.0, 0.0
+    for T in range(2 ** (n - 1)):
+        d = [1 if (j == n - 1 or (T >> j) & 1) else -1 for j in range(n)]
+        xs = [sum(complex(A[i, j]) * d[j] for j in range(n)) / 2 for i in range(n)] if cplx else \
+            [float(sum(Fraction(float(A[i, j])) * d[j] for j in range(n)) / 2) for i in range(n)]
+        mags = [abs(x) for x in xs]
+        S += math.prod(mags)
+        W += math.fsum(R[i] * math.prod(mags[:i] + mags[i + 1:]) for i in range(n))
+    return S, W
+
+
+@pytest.mark.parametrize("n", [1, 2, 4, 7, 9])
+def test_dd_stats_sum_and_magnitudes_by_definition(oracle, n):
+    A = syn.signed_real(n, 5500 + n)
+    N = 2 ** (n - 1)
+    r = oracle.ryser_dd_stats_range(A, 0, N, threads=3)
+    exact = oracle.perm_bruteforce(A) if n <= 8 else None
+    if exact is not None:
+        got = (Fraction(r["hi"]) + Fraction(r["lo"])) * 2 * (-1) ** (n - 1)
+        assert abs(got - exact) <= Fraction(1, 10 ** 27) * Fraction(_perm_abs(A))
+    S, W = _stats_by_definition(A)
+    assert r["S"] == pytest.approx(S, rel=1e-13)
+    assert r["W"] == pytest.approx(W, rel=1e-13)
+    # the sum is the one of ryser_dd_range, range by range
+    for g0, g1 in ((0, N), (0, 1), (N // 3, N)):
+        s = oracle.ryser_dd_stats_range(A, g0, g1, threads=2)
+        assert (s["hi"], s["lo"]) == oracle.ryser_dd_range(A, g0, g1, threads=2)
+
+
+@pytest.mark.parametrize("n", [5, 8, 12, 21])
+def test_dd_stats_all_equal_closed_forms(oracle, n):
+    """a J_n: x_i = a (|T| + 1 - n/2) for every row, so
+    S = a^n sum_k C(n-1, k) |k + 1 - n/2|^n and, with R_i = n |a|,
+    W = n (n |a|) |a|^(n-1) sum_k C(n-1, k) |k + 1 - n/2|^(n-1)."""
+    a = 0.75
+    r = oracle.ryser_dd_stats_range(syn.constant(n, a), 0, 2 ** (n - 1), threads=4)
+    s = sum(math.comb(n - 1, k) * abs(k + 1 - n / 2) ** n for k in range(n)) * a ** n
+    w = n * n * a * a ** (n - 1) * sum(math.comb(n - 1, k) * abs(k + 1 - n / 2) ** (n - 1) for k in range(n))
+    assert r["S"] == pytest.approx(s, rel=1e-13)
+    assert r["W"] == pytest.approx(w, rel=1e-13)
+    exact = Fraction(math.factorial(n)) * Fraction(a) ** n
+    got = (Fraction(r["hi"]) + Fraction(r["lo"])) * 2 * (-1) ** (n - 1)
+    assert abs(got - exact) <= Fraction(1, 10 ** 26) * exact
+
+
+def _gaussian_integer_matrix(n, seed):
+    g = np.random.default_rng(seed)
+    return (g.integers(-3, 4, (n, n)) + 1j * g.integers(-3, 4, (n, n))).astype(np.complex128)
+
+
+@pytest.mark.parametrize("n", range(1, 8))
+def test_cdd_exact_on_gaussian_integers(oracle, n):
+    """Gaussian-integer entries: every x_i is a multiple of 1/2 and every product
+    is exact in double-double, so the sweep equals Eq. 1 summed exactly."""
+    A = _gaussian_integer_matrix(n, 5600 + n)
+    re, im = oracle.perm_bruteforce(A.tolist())
+    r = oracle.ryser_cdd_range(A, 0, 2 ** (n - 1), threads=2)
+    f = 2 * (-1) ** (n - 1)
+    assert (Fraction(r["re_hi"]) + Fraction(r["re_lo"])) * f == re
+    assert (Fraction(r["im_hi"]) + Fraction(r["im_lo"])) * f == im
+
+
+@pytest.mark.parametrize("n", [3, 6, 8])
+def test_cdd_magnitudes_by_definition(oracle, n):
+    A = syn.complex_uniform(n, 5700 + n)
+    r = oracle.ryser_cdd_range(A, 0, 2 ** (n - 1), threads=3)
+    S, W = _stats_by_definition(A)
+    assert r["S"] == pytest.approx(S, rel=1e-12)
+    assert r["W"] == pytest.approx(W, rel=1e-12)
+
+
+def test_cdd_special_cases(oracle):
+    """Zero imaginary parts reduce to the real double-double sweep; a Haar unitary
+    matches the subset expansion of Eq. 1 and |perm(U)| <= 1; conj(U) gives the
+    conjugate; a range partition adds up to the full sum."""
+    A = syn.signed_real(11, 5800)
+    N = 2 ** 10
+    r = oracle.ryser_cdd_range(A.astype(np.complex128), 0, N, threads=2)
+    d = oracle.ryser_dd_range(A, 0, N, threads=2)
+    assert (r["re_hi"], r["re_lo"]) == d and r["im_hi"] == 0.0 and r["im_lo"] == 0.0
+    U = syn.haar_unitary(12, 5801)
+    r = oracle.ryser_cdd_range(U, 0, 2 ** 11)
+    p = complex(r["re_hi"] + r["re_lo"], r["im_hi"] + r["im_lo"]) * -2
+    assert abs(p - oracle.perm_dp_c128(U)) <= 1e-13 and abs(p) <= 1.0
+    q = oracle.ryser_cdd_range(np.conj(U), 0, 2 ** 11)
+    assert (q["re_hi"], q["re_lo"]) == (r["re_hi"], r["re_lo"])
+    assert (q["im_hi"], q["im_lo"]) == (-r["im_hi"], -r["im_lo"])
+    parts = [oracle.ryser_cdd_range(U, a, b, threads=2) for a, b in ((0, 5), (5, 1000), (1000, 2 ** 11))]
+    tot = sum(Fraction(p["re_hi"]) + Fraction(p["re_lo"]) for p in parts)
+    assert abs(float(tot) - (r["re_hi"] + r["re_lo"])) <= 1e-28
