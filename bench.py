@@ -171,24 +171,19 @@ def run_reference(args):
 
 # ------------------------------------------------------------------- GPU arm
 
-def profiled_traffic(kernel_file: str, summary: str):
-    """DRAM bytes per launch recorded in a committed ncu summary, if the kernel
-    source it was taken from is unchanged (the summary carries its hash)."""
+# Executed lane-instructions per Gray step of ryser_real_kernel<40>, from an ncu
+# capture of this kernel (smsp__inst_executed.sum x 32 / steps), with the
+# SHA-256 (first 16 hex digits) of the kernel source it was taken on.  The
+# issue view below is reported only while real.cuh still has that hash.
+REAL40_INST_PER_STEP = None
+REAL40_INST_SOURCE = None
+
+
+def kernel_source_hash() -> str:
     import hashlib
 
-    try:
-        text = open(os.path.join(ROOT, "profiles", summary)).read()
-        src = open(os.path.join(ROOT, "paper_2502_16577_gb300", "csrc", kernel_file), "rb").read()
-    except OSError:
-        return None
-    digest = hashlib.sha256(src).hexdigest()[:16]
-    traffic, tag = None, None
-    for line in text.splitlines():
-        if line.startswith("dram_bytes_per_launch:"):
-            traffic = float(line.split(":", 1)[1])
-        if line.startswith("source_sha256_16:"):
-            tag = line.split(":", 1)[1].strip()
-    return traffic if tag == digest else None
+    with open(os.path.join(ROOT, "paper_2502_16577_gb300", "csrc", "real.cuh"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
 def host_cpu() -> str:
@@ -275,6 +270,15 @@ def run_gpu(args):
         st = int(m["status"].item())
         if st not in (0,):
             raise RuntimeError(f"{m['name']}: status {st}")
+        m["ref"] = m["out"].clone()  # the kernels are deterministic: every timed step must match
+
+    def verify_step():
+        for m in mats:
+            st = int(m["status"].item())
+            if st != 0:
+                raise RuntimeError(f"timed step: {m['name']} status {st}")
+            if not torch.equal(m["out"], m["ref"]):
+                raise RuntimeError(f"timed step: {m['name']} result differs from the warm-up's bits")
 
     peaks = pg.pipe_peaks(stream) if rank == 0 else {}
 
@@ -291,6 +295,7 @@ def run_gpu(args):
         one_step((r0, r1))
         e1.record(stream)
         torch.cuda.synchronize(dev)
+        verify_step()
         gather_and_combine()
         step_ms.append(e0.elapsed_time(e1))
         real_ms.append(r0.elapsed_time(r1))
@@ -313,12 +318,14 @@ def run_gpu(args):
         host = [(m["host"], m["n"]) for m in mats]
         h2d = sum(a.nbytes for a, _ in host)
         d2h = 8 + 16 + 16
-        ke = max(1, min(args.steps, 2))
+        ke = args.steps
+        want = [pg.perm_host(a) for a, _ in host]  # untimed: the values every timed step must return
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         for _ in range(ke):
-            for a, _ in host:
-                pg.perm_host(a)
+            got = [pg.perm_host(a) for a, _ in host]
+            if got != want:
+                raise RuntimeError("e2e: a host-buffer step returned other values")
         dt = time.perf_counter() - t0
         e2e = {"value": total_steps * ke / dt, "unit": "steps/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
@@ -329,11 +336,15 @@ def run_gpu(args):
     batched = None if args.no_batched else measure_batched(pg, dev, stream)
     grad = None if args.no_batched else measure_grad(pg, dev, stream)
 
-    # roofline of the dominant kernel (dense real n=40): issue-slot work of the
-    # integer factor sequence against the SM issue peak; FP64 view alongside
+    extras = None if args.no_batched else measure_extras(pg, dev, stream)
+
+    # roofline of the dominant kernel (dense real n=40).  The method's work is
+    # 2n operations per Gray step (n row updates and n factors of the product,
+    # Alg. 1); the kernel runs them on the integer pipes, so the ceiling is the
+    # SM issue rate (152 SMs x 128 lanes x the maximum SM clock).
     n40 = 40
-    per_step_slots = 14 * n40 + 10
-    real_s = statistics.mean(real_ms) * 1e-3
+    method_ops = 2 * n40
+    real_s = statistics.median(real_ms) * 1e-3
     real_steps = mats[0]["hi"] - mats[0]["lo"]
     mp = measured_peaks()
     sm_max = float(mp.get("sm_max_mhz", 2070.0))
@@ -341,9 +352,13 @@ def run_gpu(args):
 
     nsm = _t.cuda.get_device_properties(dev).multi_processor_count
     issue_peak = nsm * 128 * sm_max * 1e6  # lane-instructions/s
-    achieved = per_step_slots * real_steps / real_s
+    achieved = method_ops * real_steps / real_s
     fp64_peak = peaks.get("fp64_fma", 0.0)  # FP64 instructions/s (an FMA counts once)
-    fp64_equiv = 2 * n40 * real_steps / real_s
+    issue_view = None
+    if REAL40_INST_PER_STEP and REAL40_INST_SOURCE == kernel_source_hash():
+        issue_view = {"inst_per_step": REAL40_INST_PER_STEP,
+                      "issue_frac": REAL40_INST_PER_STEP * real_steps / real_s / issue_peak,
+                      "source": "ncu smsp__inst_executed.sum of this kernel source"}
     line = {
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": local_ms / args.steps, "higher_is_better": True,
@@ -355,17 +370,20 @@ def run_gpu(args):
                    "binary64 + double-double sums; 0/1 exact mod 2^192"},
         "gpu_launches": 3 * args.steps,
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": issue_peak / 1e12,
-                     "unit": "Tinst/s", "frac": achieved / issue_peak,
-                     "traffic": args.traffic if args.traffic is not None else
-                     profiled_traffic("real.cuh", "ryser_real_kernel_n40.md"),
-                     "kernel": "ryser_real_kernel<40>", "work_per_step": per_step_slots,
-                     "peak_from": f"{nsm} SMs x 128 issue lanes x {sm_max:.0f} MHz (max SM clock)"},
-        "fp64_view": {"steps_per_s": real_steps / real_s, "fp64_equiv_ops_per_s": fp64_equiv,
+                     "unit": "Tops/s", "frac": achieved / issue_peak, "traffic": args.traffic,
+                     "kernel": "ryser_real_kernel<40>", "work_per_step": method_ops,
+                     "work": "2n method operations per Gray step (Alg. 1: n row updates, n product factors)",
+                     "peak_from": f"{nsm} SMs x 128 issue lanes x {sm_max:.0f} MHz (max SM clock)",
+                     "issue_view": issue_view},
+        "fp64_view": {"steps_per_s": real_steps / real_s, "fp64_equiv_ops_per_s": method_ops * real_steps / real_s,
                       "fp64_pipe_peak_ops_per_s": fp64_peak,
-                      "frac_of_fp64_peak": fp64_equiv / fp64_peak if fp64_peak else None,
+                      "fp64_equiv_rate_over_fp64_peak": method_ops * real_steps / real_s / fp64_peak
+                      if fp64_peak else None,
+                      "note": "the 2n operations per step run on the integer pipes, not the FP64 pipe",
                       "paper_gv100_steps_per_s": 2 ** 39 / 14.17},
         "pipe_peaks": peaks,
-        "per_config_ms": {"real40": statistics.mean(real_ms)},
+        "per_config_ms": {"real40": statistics.median(real_ms)},
+        "extras": extras,
         "batched": batched,
         "grad": grad,
         "clocks": clocks,
@@ -380,93 +398,123 @@ def run_gpu(args):
     return 0
 
 
-def measure_batched(pg, dev, stream, count: int = 8192):
+def _median_ms(fn, sync, ev, stream, reps: int = 5, check=None):
+    """Median device time (CUDA events on the stream) of reps calls of fn, after
+    one untimed call; check() runs after every timed call."""
+    fn()
+    sync()
+    if check:
+        check()
+    ts = []
+    for _ in range(reps):
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        sync()
+        if check:
+            check()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def measure_batched(pg, dev, stream, count: int = 8192, reps: int = 5):
     """Batched boson workload: 8192 complex k x k submatrices (k uniform in
-    8..26, rows with replacement from a Haar 256 x 256 unitary): one graph
-    replay of the batched plan, with the drawn modes as row labels (repeated
-    rows summed over their multiplicities) and without them, vs a loop of
-    perm() launches on one stream."""
+    8..26, rows with replacement from a Haar 256 x 256 unitary): graph replays
+    (median of reps) of the plan with the heuristic chunking, and of the plan
+    with the drawn modes as row labels (repeated rows summed over their
+    multiplicities), heuristic and autotuned (perm_batched_autotune, one
+    round), against a loop of perm() launches on one stream.  Every replay's
+    statuses and bits are checked."""
     import torch
 
     mats, rows = syn.batched_boson(count, with_rows=True)
     ev = lambda: torch.cuda.Event(enable_timing=True)
-    e0, e1 = ev(), ev()
+    sync = lambda: torch.cuda.synchronize(dev)
 
-    def replay(plan):
-        plan.run(stream)  # warm-up
-        e0.record(stream)
-        plan.run_async(stream)
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        t = e0.elapsed_time(e1) * 1e-3
-        return t, plan.run(stream)
+    def timed_plan(plan):
+        ref = plan.run(stream)
+
+        def check():
+            if not bool((plan.status == 0).all()):
+                raise RuntimeError("batched replay: a nonzero status")
+            o = plan.out.cpu().numpy()
+            if not np.array_equal(o[0::2] + 1j * o[1::2], ref):
+                raise RuntimeError("batched replay: results differ between replays")
+
+        ms = _median_ms(lambda: plan.run_async(stream), sync, ev, stream, reps, check)
+        return ms * 1e-3, ref
 
     plan = pg.BatchPlan(mats, device=dev)
-    t_plain, res = replay(plan)
+    t_plain, res = timed_plan(plan)
     plan.close()
     plan = pg.BatchPlan(mats, device=dev, row_labels=rows)
-    t_graph, res_lab = replay(plan)
+    t_lab, res_lab = timed_plan(plan)
+    plan.close()
+    t0 = time.perf_counter()
+    plan = pg.BatchPlan(mats, device=dev, row_labels=rows, autotune_rounds=1, stream=stream)
+    tune_lab_s = time.perf_counter() - t0
+    t_lab_tuned, _ = timed_plan(plan)
     plan.close()
     devm = [torch.from_numpy(np.ascontiguousarray(m)).to(dev) for m in mats]
     out = torch.zeros(2 * count, dtype=torch.float64, device=dev)
     st = torch.zeros(count, dtype=torch.int32, device=dev)
-    for i in range(64):
-        pg.perm_async(devm[i], out[2 * i:2 * i + 2], st[i:i + 1], stream)
-    torch.cuda.synchronize(dev)
-    e0.record(stream)
-    for i in range(count):
-        pg.perm_async(devm[i], out[2 * i:2 * i + 2], st[i:i + 1], stream)
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    t_loop = e0.elapsed_time(e1) * 1e-3
+
+    def loop():
+        for i in range(count):
+            pg.perm_async(devm[i], out[2 * i:2 * i + 2], st[i:i + 1], stream)
+
+    def check_loop():
+        if not bool((st == 0).all()):
+            raise RuntimeError("perm() loop: a nonzero status")
+
+    t_loop = _median_ms(loop, sync, ev, stream, 3, check_loop) * 1e-3
     o = out.cpu().numpy()
     same = bool(np.array_equal(res, o[0::2] + 1j * o[1::2]))
     scale = np.maximum(np.abs(res), 1e-300)
     steps = sum(1 << (m.shape[0] - 1) for m in mats)
+    best = min(t_lab, t_lab_tuned)
     return {"workload": f"{count} complex128 boson submatrices, k uniform 8..26, drawn modes as row labels",
-            "perms_per_s": count / t_graph, "plain_perms_per_s": count / t_plain,
+            "perms_per_s": count / best, "labeled_perms_per_s": count / t_lab,
+            "labeled_autotuned_perms_per_s": count / t_lab_tuned,
+            "plain_perms_per_s": count / t_plain, "autotune_seconds": tune_lab_s,
             "steps_per_s": steps / t_plain, "loop_perms_per_s": count / t_loop,
-            "speedup_vs_loop": t_loop / t_graph, "labeled_vs_plain_max_rel": float(np.max(np.abs(res_lab - res) / scale)),
-            "plain_identical_to_loop": same, "launches_per_replay": 3}
+            "speedup_vs_loop": t_loop / best,
+            "labeled_vs_plain_max_rel": float(np.max(np.abs(res_lab - res) / scale)),
+            "plain_identical_to_loop": same, "launches_per_replay": 3, "timing": f"median of {reps} replays"}
 
 
-def measure_grad(pg, dev, stream, reps: int = 3):
+def measure_grad(pg, dev, stream, reps: int = 5):
     """Fused gradient: dense real n=28 uniform [-1, 1) (perm_grad vs perm on the
     same matrix, and vs n^2 forwards of one (n-1) minor), and 1024 complex
-    16 x 16 Haar submatrices (perm_grad_batched vs the batched forward plan)."""
+    16 x 16 Haar submatrices (perm_grad_batched vs the batched forward plan).
+    Medians of reps launches; statuses checked after each."""
     import torch
 
     ev = lambda: torch.cuda.Event(enable_timing=True)
+    sync = lambda: torch.cuda.synchronize(dev)
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
 
-    def timed(fn):
-        fn()
-        torch.cuda.synchronize(dev)
-        ts = []
-        for _ in range(reps):
-            e0, e1 = ev(), ev()
-            e0.record(stream)
-            fn()
-            e1.record(stream)
-            torch.cuda.synchronize(dev)
-            ts.append(e0.elapsed_time(e1) * 1e-3)
-        return statistics.median(ts)
+    def ok():
+        if int(st.item()) != 0:
+            raise RuntimeError(f"gradient section: status {int(st.item())}")
 
     A = torch.from_numpy(syn.grad_real_28()).to(dev)
     n = A.shape[0]
     out = torch.zeros(2, dtype=torch.float64, device=dev)
     G = torch.empty_like(A)
-    st = torch.zeros(1, dtype=torch.int32, device=dev)
-    t_grad = timed(lambda: pg.perm_grad_async(A, out[:1], G, st, stream))
-    t_fwd = timed(lambda: pg.perm_async(A, out, st, stream))
+    t_grad = _median_ms(lambda: pg.perm_grad_async(A, out[:1], G, st, stream), sync, ev, stream, reps, ok) * 1e-3
+    t_fwd = _median_ms(lambda: pg.perm_async(A, out, st, stream), sync, ev, stream, reps, ok) * 1e-3
     M = A[1:, 1:].contiguous()
-    t_minor = timed(lambda: pg.perm_async(M, out, st, stream))
+    t_minor = _median_ms(lambda: pg.perm_async(M, out, st, stream), sync, ev, stream, reps, ok) * 1e-3
     mats = syn.grad_boson_16(1024)
     B = torch.from_numpy(mats).to(dev)
     bout = torch.zeros(1024, dtype=torch.complex128, device=dev)
     BG = torch.empty_like(B)
-    t_bgrad = timed(lambda: pg.perm_grad_batched_async(B, bout, BG, st, stream))
+    t_bgrad = _median_ms(lambda: pg.perm_grad_batched_async(B, bout, BG, st, stream), sync, ev, stream, reps,
+                         ok) * 1e-3
     plan = pg.BatchPlan(list(mats), device=dev)
-    t_bfwd = timed(lambda: plan.run_async(stream))
+    t_bfwd = _median_ms(lambda: plan.run_async(stream), sync, ev, stream, reps) * 1e-3
     plan.close()
     k = mats.shape[1]
     return {"real28": {"grad_ms": t_grad * 1e3, "fwd_ms": t_fwd * 1e3, "grad_over_fwd": t_grad / t_fwd,
@@ -476,7 +524,38 @@ def measure_grad(pg, dev, stream, reps: int = 3):
             "complex16_x1024": {"grad_ms": t_bgrad * 1e3, "fwd_ms": t_bfwd * 1e3,
                                 "grad_over_fwd": t_bgrad / t_bfwd,
                                 "steps_per_s": 1024 * (1 << (k - 1)) / t_bgrad},
+            "timing": f"median of {reps} launches",
             "launches": "grad: 1 sweep + 3 small finishing kernels; fwd: 1 (real), 3 per graph replay (batched)"}
+
+
+def measure_extras(pg, dev, stream, reps: int = 5):
+    """The other named workloads: the sparse n = 44 matrix (density 0.2) on a
+    fixed 2^36-step sub-range of its sweep (every chunk the same work), and the
+    latency of one dense real n = 24 uniform [0, 1) permanent (2^23 steps, too
+    small to fill the GPU).  Medians of reps launches, statuses checked."""
+    import torch
+
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    sync = lambda: torch.cuda.synchronize(dev)
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+
+    def ok():
+        if int(st.item()) != 0:
+            raise RuntimeError(f"extras: status {int(st.item())}")
+
+    S = syn.sparse_44()
+    cp, ri, cv = (torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in syn.to_ccs(S))
+    part = torch.zeros(2, dtype=torch.float64, device=dev)
+    g0, g1 = 1 << 40, (1 << 40) + (1 << 36)
+    t_sp = _median_ms(lambda: pg.perm_sparse_range_async(44, cp, ri, cv, g0, g1, part, st, stream), sync, ev,
+                      stream, reps, ok) * 1e-3
+    A = torch.from_numpy(syn.dense_real_24()).to(dev)
+    out = torch.zeros(1, dtype=torch.float64, device=dev)
+    lat = _median_ms(lambda: pg.perm_async(A, out, st, stream), sync, ev, stream, 4 * reps, ok)
+    return {"sparse44": {"steps": g1 - g0, "ms": t_sp * 1e3, "steps_per_s": (g1 - g0) / t_sp,
+                         "nnz": int(ri.numel()), "full_sweep_s_estimate": (1 << 43) / ((g1 - g0) / t_sp)},
+            "dense24": {"latency_ms": lat, "steps_per_s": (1 << 23) / (lat * 1e-3)},
+            "timing": f"median of {reps} (dense24: {4 * reps}) launches"}
 
 
 def run_case(args):

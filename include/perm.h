@@ -44,7 +44,7 @@
 extern "C" {
 #endif
 
-#define PERM_ABI_VERSION 3
+#define PERM_ABI_VERSION 4
 #define PERM_NMAX 63
 
 typedef enum {
@@ -63,7 +63,8 @@ typedef enum {
   PERM_EOVERFLOW = 3, /* BIN: the permanent may not fit 128 bits              */
   PERM_ECUDA = 4,     /* a CUDA call failed                                    */
   PERM_ENOMEM = 5,    /* scratch allocation failed                             */
-  PERM_EABORTED = 6   /* stopped early by the word of perm_set_abort_word      */
+  PERM_EABORTED = 6,  /* stopped early by the word of perm_set_abort_word      */
+  PERM_ETIMEOUT = 7   /* stopped when the budget of perm_set_time_budget ran out */
 } perm_status_t;
 
 /*
@@ -145,6 +146,27 @@ int perm_sparse(int n, const int32_t* cptrs, const int32_t* rids, const double* 
                 double* out, int32_t* status, void* stream);
 
 /*
+ * perm_sparse_range - the unscaled partial sum of the sparse sweep over the
+ * steps g in [g_begin, g_end) (0 <= g_begin <= g_end <= 2^(n-1)), written to
+ * partial (device double[2] = (hi, lo)), for splitting one sparse permanent
+ * over GPUs, processes or time like perm_range (Secs. 3.3 and 6.3).
+ *   flags 0: the kernel's own column order.  Up to four sparse columns
+ *       (chosen from the matrix alone, deterministically) take Gray bits
+ *       0..B-1 so that the rows they do not touch stay constant for 2^B steps
+ *       (a column permutation leaves the permanent unchanged); the remaining
+ *       columns follow in their order.  Partials of any partition of
+ *       [0, 2^(n-1)) made with flags 0 combine to perm(A), as perm_sparse.
+ *   flags PERM_SPARSE_PAPER_ORDER: Alg. 2's own order, Gray bit j <-> column j
+ *       (the steps of perm_range on the dense form); slower at low density.
+ * Partials combine with perm_combine(PERM_F64, ...).  status as perm_sparse;
+ * PERM_EINVAL for unknown flags, PERM_ERANGE for a bad range.
+ */
+#define PERM_SPARSE_PAPER_ORDER 1
+int perm_sparse_range(int n, const int32_t* cptrs, const int32_t* rids, const double* cvals, int64_t nnz,
+                      uint64_t g_begin, uint64_t g_end, int flags, double* partial, int32_t* status,
+                      void* stream);
+
+/*
  * Batched permanents (boson-sampling style: thousands of small k x k
  * matrices of uneven sizes; complex, or real).  Each matrix is the sweep of perm() (Alg. 1 over
  * complex entries, Alg. 3 chunks of Sec. 3.1.1); all of them run in one
@@ -164,8 +186,8 @@ int perm_sparse(int n, const int32_t* cptrs, const int32_t* rids, const double* 
  *     out        device; PERM_C128: double[2*count], (re, im) of perm of
  *                every matrix; PERM_F64: double[count].
  *     status     device int32[count] or NULL (perm() status per matrix).
- *   A_packed, out and status are bound to the plan: every perm_batched()
- *   replay reads and writes these buffers.
+ *   A_packed, out and status are the plan's default buffers: a
+ *   perm_batched() call that passes NULL for one of them uses the default.
  * perm_batched_plan_create_labeled - the same, with row_labels_host (host
  *   int32[sum of ns], the rows of matrix 0, then matrix 1, ...): rows of one
  *   matrix with equal labels must be equal (checked on the device: PERM_EINVAL
@@ -190,6 +212,15 @@ int perm_sparse(int n, const int32_t* cptrs, const int32_t* rids, const double* 
  *   c times to every column sum (x_j = (a_fj + sum_r c a_rj + sum_t d_t a_tj) / 2,
  *   d_t = -1 at step 0).  -PERM_ENOMEM if desc_cap is too small.
  * perm_batched - replay the plan's graph on stream (allocates nothing).
+ *   A_packed, out, status: device buffers of this call, laid out as at plan
+ *   creation (the same sizes, the same element offsets of every matrix); NULL
+ *   selects the plan's default buffer.  When they (or the registered abort
+ *   word or time budget) differ from the previous replay's, the kernel nodes
+ *   of the instantiated graph are updated in place before the launch
+ *   (cudaGraphExecKernelNodeSetParams): no capture, no allocation, no wait.
+ *   Replays of one plan must be ordered (they share the plan's work queue and
+ *   partial sums).  A stopped replay (abort word, time budget) reports
+ *   PERM_EABORTED / PERM_ETIMEOUT for every matrix, out NaN.
  * perm_batched_autotune - time the candidate chunk exponents and the
  *   one-matrix-per-lane mode of every size class on the plan's own matrices
  *   (rounds timed runs each), keep the fastest, rebuild the queue and
@@ -206,7 +237,7 @@ int perm_batched_plan_create_labeled(perm_batch_plan** plan, int type, const int
                                      const int32_t* row_labels_host);
 int perm_batched_units(int k, const int32_t* labels, int max_units, int32_t* gray_bits, double* weight,
                        int32_t* desc, int desc_cap, int32_t* desc_off);
-int perm_batched(perm_batch_plan* plan, void* stream);
+int perm_batched(perm_batch_plan* plan, const void* A_packed, void* out, int32_t* status, void* stream);
 int perm_batched_autotune(perm_batch_plan* plan, int rounds, void* stream);
 int perm_batched_plan_info(const perm_batch_plan* plan, int k, int* mode, int* c, int* nitems);
 void perm_batched_plan_destroy(perm_batch_plan* plan);
@@ -250,11 +281,35 @@ int perm_grad_batched(const void* A, int n, int count, int type, void* out, void
  *   status        optional device int32: the first failing order's code.
  * The host groups the matrices by order; each group is gathered into a
  * contiguous batch, swept by one perm_grad_batched launch and scattered
- * back.  Allocates a workspace and waits for the stream before returning.
+ * back.  A one-shot gradient plan (below): allocates its buffers and waits
+ * for the stream before returning; use a plan to avoid both.
  */
 int perm_grad_batched_mixed(int type, const int* ns_host, int count, const void* A_packed,
                             const int64_t* offsets_host, void* out, void* G_packed, int32_t* status,
                             void* stream);
+
+/*
+ * Gradient plans: perm_grad_batched_mixed without allocation or waiting per
+ * call, for training loops that evaluate the same shapes many times.
+ * perm_grad_plan_create - (host call, synchronous) group `count` matrices of
+ *   orders ns_host[m] (0..32) at element offsets offsets_host[m] (the layout of
+ *   perm_grad_batched_mixed), choose each group's launch shape and allocate
+ *   every device buffer the runs need (gather / scatter buffers, index arrays,
+ *   one sweep workspace shared by the groups).
+ * perm_grad_plan_run - for caller buffers A_packed, G_packed (same offsets)
+ *   and out (count elements): per order, gather, one fused sweep
+ *   (perm_grad_batched's kernels), scatter; then the status (the first
+ *   failing order's code).  Stream-ordered: no allocation, no wait.  Runs of
+ *   one plan must be ordered (they share its buffers).
+ * perm_grad_plan_destroy - free the plan (NULL is ignored); call it after the
+ *   plan's last run has completed.
+ */
+typedef struct perm_grad_plan perm_grad_plan;
+int perm_grad_plan_create(perm_grad_plan** plan, int type, const int* ns_host, int count,
+                          const int64_t* offsets_host);
+int perm_grad_plan_run(perm_grad_plan* plan, const void* A_packed, void* out, void* G_packed, int32_t* status,
+                       void* stream);
+void perm_grad_plan_destroy(perm_grad_plan* plan);
 
 /*
  * Sparse preprocessing (Sec. 4; host-side graph work, leaves on the GPU).
@@ -328,7 +383,8 @@ int perm_f64_noalloc(const double* A, int n, double* out, int32_t* status, void*
  * of 256 threads per SM, best of 3) and writes lane-instructions per second:
  *   out[0] fma.rn.f64, out[1] add.rn.f64, out[2] mad.lo.u32,
  *   out[3] mad.wide.u32, out[4] shf.l.wrap.b32  (first count entries).
- *   out  host double[count], 1 <= count <= 5.  Waits for the stream.
+ *   out  host double[count], 1 <= count <= 5; an entry that could not be
+ *        timed (a CUDA error) is NaN.  Waits for the stream.
  */
 int perm_pipe_peaks(double* out, int count, void* stream);
 
@@ -336,17 +392,35 @@ int perm_pipe_peaks(double* out, int count, void* stream);
  * Cancellation (no counterpart in the paper; a service around Alg. 3's chunk
  * loop).  perm_set_abort_word registers a word of page-locked MAPPED host
  * memory (cudaHostAlloc with cudaHostAllocMapped, or perm_abort_word_alloc);
- * NULL unregisters it.  The sweeps of perm, perm_range, perm_sparse and
- * perm_f64_noalloc launched afterwards read it once per chunk group and warp;
- * when it is nonzero they stop and report PERM_EABORTED (out NaN, or zero for
- * 0/1).  Setting the word to nonzero from the host while a launch runs ends
- * that launch early.  Nothing waits on the word.  Returns PERM_EINVAL when
- * the pointer is not mapped host memory.  One word for the process; the
- * batched and gradient launches do not read it.
+ * NULL unregisters it.  The sweeps of perm, perm_range, perm_sparse,
+ * perm_sparse_range and perm_f64_noalloc launched afterwards read it once per
+ * chunk group and warp, the batched replays once per work item and warp, the
+ * gradient sweeps once per block-item and CTA; when it is nonzero they stop
+ * and report PERM_EABORTED (out NaN, or zero for 0/1; a batched replay marks
+ * every matrix of the plan).  Setting the word to nonzero from the host while
+ * a launch runs ends that launch early.  Nothing waits on the word.  Returns
+ * PERM_EINVAL when the pointer is not mapped host memory.  One word for the
+ * process, read at every launch (a batched plan reads it at every
+ * perm_batched call).
  * perm_abort_word_alloc / perm_abort_word_free - allocate (zeroed) / free
  * such a word (freeing the registered word unregisters it).
  */
 int perm_set_abort_word(volatile uint32_t* host_mapped);
+
+/*
+ * perm_set_time_budget - a time budget for every sweep launched afterwards
+ * (the paper's largest run took 1.63 days, Secs. 1 and 6.3; a service needs a
+ * bound).  Each warp reads the GPU's nanosecond timer between its chunk groups
+ * (Alg. 3's chunk loop) and stops once more than `nanoseconds` have passed
+ * since it started; the launch then reports PERM_ETIMEOUT (out NaN, or zero
+ * for 0/1), its partial results discarded.  Work already done in a group
+ * finishes, so a launch overruns its budget by at most one chunk group.
+ * 0 (the default) means no budget.  One budget for the process; it applies to
+ * perm, perm_range, perm_sparse, perm_sparse_range, perm_f64_noalloc, the
+ * batched replays and the gradient sweeps, like the abort word.  Returns
+ * PERM_OK.
+ */
+int perm_set_time_budget(uint64_t nanoseconds);
 int perm_abort_word_alloc(volatile uint32_t** host_word);
 int perm_abort_word_free(volatile uint32_t* host_word);
 

@@ -19,10 +19,12 @@ import ctypes
 import numpy as np
 
 from . import _lib
-from ._lib import PERM_BIN, PERM_C128, PERM_EABORTED, PERM_F64, PERM_F64X, PermError, check, load
+from ._lib import (PERM_BIN, PERM_C128, PERM_EABORTED, PERM_EINVAL, PERM_ENOMEM, PERM_EOVERFLOW, PERM_ERANGE,
+                   PERM_ETIMEOUT, PERM_F64, PERM_F64X, PERM_OK, PermError, check, load)
 
-__all__ = ["perm", "perm_async", "perm_range", "perm_range_async", "perm_combine", "perm_sparse", "perm_sparse_async", "perm_host", "pipe_peaks", "BatchPlan", "AbortWord", "perm_grad", "perm_grad_async", "perm_grad_batched", "perm_grad_batched_async", "perm_grad_mixed", "permanent", "batched_units", "equal_row_labels", "perm_type_of", "PermError",
-           "PERM_F64", "PERM_C128", "PERM_BIN", "PERM_F64X", "perm_x", "PERM_EABORTED", "load"]
+__all__ = ["perm", "perm_async", "perm_range", "perm_range_async", "perm_combine", "perm_sparse", "perm_sparse_async", "perm_sparse_range", "perm_sparse_range_async", "perm_host", "pipe_peaks", "BatchPlan", "AbortWord", "perm_grad", "perm_grad_async", "perm_grad_batched", "perm_grad_batched_async", "perm_grad_mixed", "GradPlan", "set_time_budget", "permanent", "batched_units", "equal_row_labels", "perm_type_of", "PermError",
+           "PERM_F64", "PERM_C128", "PERM_BIN", "PERM_F64X", "perm_x", "PERM_EABORTED", "PERM_ETIMEOUT", "PERM_OK", "PERM_EINVAL", "PERM_ERANGE", "PERM_EOVERFLOW", "PERM_ENOMEM",
+           "load"]
 
 
 def _torch():
@@ -206,6 +208,39 @@ def perm_sparse_async(n: int, cptrs, rids, cvals, out, status=None, stream=None)
     check(rc, "perm_sparse")
 
 
+def perm_sparse_range_async(n: int, cptrs, rids, cvals, g_begin: int, g_end: int, out, status=None, stream=None,
+                            paper_order: bool = False) -> None:
+    """Enqueue the raw partial of the sparse sweep over steps [g_begin, g_end)
+    into out (float64[2] = hi, lo); paper_order selects Alg. 2's own column
+    order instead of the kernel's quiet-row order."""
+    lib = load()
+    torch = _torch()
+    for t, dt in ((cptrs, torch.int32), (rids, torch.int32), (cvals, torch.float64)):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != dt or not t.is_contiguous():
+            raise TypeError("CCS arrays must be contiguous CUDA tensors (int32, int32, float64)")
+    h, _ = _stream_handle(stream)
+    rc = lib.perm_sparse_range(int(n), ctypes.c_void_p(cptrs.data_ptr()), ctypes.c_void_p(rids.data_ptr()),
+                               ctypes.c_void_p(cvals.data_ptr()), int(rids.numel()), int(g_begin), int(g_end),
+                               _lib.PERM_SPARSE_PAPER_ORDER if paper_order else 0, ctypes.c_void_p(out.data_ptr()),
+                               ctypes.c_void_p(status.data_ptr() if status is not None else 0), h)
+    check(rc, "perm_sparse_range")
+
+
+def perm_sparse_range(n: int, cptrs, rids, cvals, g_begin: int, g_end: int, stream=None,
+                      paper_order: bool = False) -> tuple:
+    """Raw partial (hi, lo) of the sparse sweep over steps [g_begin, g_end); waits."""
+    torch = _torch()
+    dev = cptrs.device
+    out = torch.zeros(2, dtype=torch.float64, device=dev)
+    status = torch.full((1,), -1, dtype=torch.int32, device=dev)
+    perm_sparse_range_async(n, cptrs, rids, cvals, g_begin, g_end, out, status, stream, paper_order)
+    _, s = _stream_handle(stream)
+    s.synchronize()
+    check(int(status.item()), "perm_sparse_range")
+    o = out.cpu().numpy()
+    return float(o[0]), float(o[1])
+
+
 def perm_sparse(n: int, cptrs, rids, cvals, stream=None) -> float:
     """Permanent of an n x n real matrix in CCS form (Alg. 2); waits for it."""
     torch = _torch()
@@ -316,6 +351,56 @@ def perm_grad_mixed(mats, device=None, stream=None):
     check(int(status.item()), "perm_grad_batched_mixed")
     g = G.cpu().numpy()
     return out.cpu().numpy(), [g[o:o + n * n].reshape(n, n) for o, n in zip(offs, ns)]
+
+
+class GradPlan:
+    """Permanents and gradients of a fixed list of matrix orders (all float64 or
+    all complex128) through perm_grad_plan_*: the device buffers are allocated
+    once here; run() gathers, sweeps and scatters without allocating or
+    waiting.  A_packed / G_packed hold matrix m at element offsets[m]."""
+
+    def __init__(self, ns, complex_=False, offsets=None):
+        lib = load()
+        self.ns = [int(n) for n in ns]
+        if offsets is None:
+            offsets, tot = [], 0
+            for n in self.ns:
+                offsets.append(tot)
+                tot += n * n
+        self.offsets = [int(o) for o in offsets]
+        self.type = PERM_C128 if complex_ else PERM_F64
+        self._plan = ctypes.c_void_p(0)
+        karr = (ctypes.c_int * max(len(self.ns), 1))(*self.ns)
+        oarr = (ctypes.c_int64 * max(len(self.ns), 1))(*self.offsets)
+        check(lib.perm_grad_plan_create(ctypes.byref(self._plan), self.type, karr, len(self.ns), oarr),
+              "perm_grad_plan_create")
+
+    def run_async(self, A_packed, out, G_packed, status=None, stream=None) -> None:
+        """Enqueue one run on device tensors (A_packed, G_packed: the packed
+        layout; out: one element per matrix)."""
+        h, _ = _stream_handle(stream)
+        check(load().perm_grad_plan_run(self._plan, ctypes.c_void_p(A_packed.data_ptr()),
+                                        ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(G_packed.data_ptr()),
+                                        ctypes.c_void_p(status.data_ptr() if status is not None else 0), h),
+              "perm_grad_plan_run")
+
+    def close(self):
+        if self._plan:
+            load().perm_grad_plan_destroy(self._plan)
+            self._plan = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def set_time_budget(seconds) -> None:
+    """Time budget of every sweep launched afterwards (perm_set_time_budget);
+    None or 0 removes it.  A sweep that runs out stops with PERM_ETIMEOUT."""
+    ns = 0 if not seconds else max(1, int(seconds * 1e9))
+    check(load().perm_set_time_budget(ns), "perm_set_time_budget")
 
 
 def _autograd_function():
@@ -499,10 +584,17 @@ class BatchPlan:
             h, _ = _stream_handle(stream)
             check(lib.perm_batched_autotune(self._plan, int(autotune_rounds), h), "perm_batched_autotune")
 
-    def run_async(self, stream=None) -> None:
-        """Replay the plan on a stream without waiting; results land in self.out."""
+    def run_async(self, stream=None, A=None, out=None, status=None) -> None:
+        """Replay the plan on a stream without waiting.  A, out, status: device
+        tensors of this call laid out like self.A / self.out / self.status
+        (default: the plan's own); results land in out."""
         h, _ = _stream_handle(stream)
-        check(load().perm_batched(self._plan, h), "perm_batched")
+        ptr = lambda t: ctypes.c_void_p(t.data_ptr() if t is not None else 0)
+        for t, ref in ((A, self.A), (out, self.out), (status, self.status)):
+            if t is not None and (not t.is_cuda or t.dtype != ref.dtype or t.numel() != ref.numel()
+                                  or not t.is_contiguous()):
+                raise ValueError("per-call buffers must match the plan's layout (dtype, size, contiguous, CUDA)")
+        check(load().perm_batched(self._plan, ptr(A), ptr(out), ptr(status), h), "perm_batched")
 
     def run(self, stream=None):
         """Replay and return a numpy array of the permanents (complex128 or float64)."""

@@ -11,17 +11,18 @@ import os
 from . import build as _build
 
 PERM_F64, PERM_C128, PERM_BIN, PERM_F64X = 0, 1, 2, 3
-PERM_OK, PERM_EINVAL, PERM_ERANGE, PERM_EOVERFLOW, PERM_ECUDA, PERM_ENOMEM, PERM_EABORTED = range(7)
+PERM_SPARSE_PAPER_ORDER = 1
+PERM_OK, PERM_EINVAL, PERM_ERANGE, PERM_EOVERFLOW, PERM_ECUDA, PERM_ENOMEM, PERM_EABORTED, PERM_ETIMEOUT = range(8)
 
 _vp = ctypes.c_void_p
 _i32p = ctypes.POINTER(ctypes.c_int32)
 _lib = None
 
-SYMBOLS = ("perm", "perm_range", "perm_combine", "perm_sparse", "perm_host", "perm_pipe_peaks",
+SYMBOLS = ("perm", "perm_range", "perm_combine", "perm_sparse", "perm_sparse_range", "perm_host", "perm_pipe_peaks",
            "perm_batched_plan_create", "perm_batched_plan_create_labeled", "perm_batched_units", "perm_batched", "perm_batched_autotune", "perm_batched_plan_info",
-           "perm_batched_plan_destroy", "perm_grad", "perm_grad_batched", "perm_grad_batched_mixed", "perm_decomp_create", "perm_decomp_info", "perm_decomp_leaf",
+           "perm_batched_plan_destroy", "perm_grad", "perm_grad_batched", "perm_grad_batched_mixed", "perm_grad_plan_create", "perm_grad_plan_run", "perm_grad_plan_destroy", "perm_decomp_create", "perm_decomp_info", "perm_decomp_leaf",
            "perm_decomp_filtered", "perm_decomp_eval", "perm_decomp_destroy", "perm_sparse_decomp",
-           "perm_set_abort_word", "perm_abort_word_alloc", "perm_abort_word_free",
+           "perm_set_abort_word", "perm_abort_word_alloc", "perm_abort_word_free", "perm_set_time_budget",
            "perm_status_string", "perm_abi_version")
 
 
@@ -64,6 +65,9 @@ def load(build_if_missing: bool = False):
     lib.perm_combine.argtypes = [ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, _vp]
     lib.perm_sparse.restype = ctypes.c_int
     lib.perm_sparse.argtypes = [ctypes.c_int, _vp, _vp, _vp, ctypes.c_int64, _vp, _vp, _vp]
+    lib.perm_sparse_range.restype = ctypes.c_int
+    lib.perm_sparse_range.argtypes = [ctypes.c_int, _vp, _vp, _vp, ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint64,
+                                      ctypes.c_int, _vp, _vp, _vp]
     lib.perm_batched_plan_create.restype = ctypes.c_int
     lib.perm_batched_plan_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                              ctypes.c_int, _vp, ctypes.POINTER(ctypes.c_int64), _vp, _vp]
@@ -74,7 +78,7 @@ def load(build_if_missing: bool = False):
     lib.perm_batched_units.restype = ctypes.c_int
     lib.perm_batched_units.argtypes = [ctypes.c_int, _vp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int, _vp]
     lib.perm_batched.restype = ctypes.c_int
-    lib.perm_batched.argtypes = [_vp, _vp]
+    lib.perm_batched.argtypes = [_vp, _vp, _vp, _vp, _vp]
     lib.perm_batched_autotune.restype = ctypes.c_int
     lib.perm_batched_autotune.argtypes = [_vp, ctypes.c_int, _vp]
     lib.perm_batched_plan_info.restype = ctypes.c_int
@@ -91,6 +95,13 @@ def load(build_if_missing: bool = False):
                                             ctypes.POINTER(ctypes.c_int64), _vp, _vp, _vp, _vp]
     _dp = ctypes.POINTER(ctypes.c_double)
     _ip = ctypes.POINTER(ctypes.c_int)
+    lib.perm_grad_plan_create.restype = ctypes.c_int
+    lib.perm_grad_plan_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                          ctypes.POINTER(ctypes.c_int64)]
+    lib.perm_grad_plan_run.restype = ctypes.c_int
+    lib.perm_grad_plan_run.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
+    lib.perm_grad_plan_destroy.restype = None
+    lib.perm_grad_plan_destroy.argtypes = [_vp]
     lib.perm_decomp_create.restype = ctypes.c_int
     lib.perm_decomp_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, _vp, _vp, _vp, ctypes.c_int64, ctypes.c_int]
     lib.perm_decomp_info.restype = ctypes.c_int
@@ -106,6 +117,8 @@ def load(build_if_missing: bool = False):
     lib.perm_sparse_decomp.restype = ctypes.c_int
     lib.perm_sparse_decomp.argtypes = [ctypes.c_int, _vp, _vp, _vp, ctypes.c_int64, _dp, ctypes.POINTER(DecompInfo),
                                        _vp]
+    lib.perm_set_time_budget.restype = ctypes.c_int
+    lib.perm_set_time_budget.argtypes = [ctypes.c_uint64]
     lib.perm_set_abort_word.restype = ctypes.c_int
     lib.perm_set_abort_word.argtypes = [_vp]
     lib.perm_abort_word_alloc.restype = ctypes.c_int

@@ -63,16 +63,19 @@ static int floor_log2_u64(uint64_t v) {
   return r;
 }
 
+// ------------------------------------------------- cancellation, time budget
+
+static std::atomic<const volatile uint32_t*> g_abort_word{nullptr};
+static std::atomic<uint64_t> g_budget_ns{0};
+
+const volatile uint32_t* current_abort_word() { return g_abort_word.load(std::memory_order_acquire); }
+
+uint64_t current_time_budget() { return g_budget_ns.load(std::memory_order_acquire); }
+
 // Chunk exponent c: aligned chunks of 2^c steps (Sec. 3.1.1).  Aim for at
 // least 64 warp-groups of 32 chunks per resident warp (tail below ~1.6%), but
 // keep 2^c >= 4n so that starting a chunk (at most n(n-c) adds) stays small
 // against its 2^c steps of n multiplies.
-// ------------------------------------------------------------ cancellation
-
-static std::atomic<const volatile uint32_t*> g_abort_word{nullptr};
-
-const volatile uint32_t* current_abort_word() { return g_abort_word.load(std::memory_order_acquire); }
-
 int plan_chunk_exponent(int n, uint64_t nsteps, int warps_resident) {
   int cmax = n - 1 < 30 ? n - 1 : 30;
   if (cmax < 0) cmax = 0;
@@ -85,25 +88,34 @@ int plan_chunk_exponent(int n, uint64_t nsteps, int warps_resident) {
   return c;
 }
 
-// One Ryser launch over [g_begin, g_end): scratch from the stream-ordered
-// allocator, arrival counter zeroed, kernel, scratch released.
-static int launch_ryser(const KernelEntry& ke, const void* A, int n, uint64_t g_begin, uint64_t g_end, int mode,
-                        void* out, int32_t* status, cudaStream_t s, size_t part_bytes) {
+int plan_ryser_launch(const KernelEntry& ke, int n, uint64_t g_begin, uint64_t g_end, RyserLaunch& L) {
   if (!ke.fn) return PERM_EINVAL;
   DeviceFacts df;
   int rc = current_device_facts(df);
   if (rc) return rc;
   int nb = blocks_per_sm(ke);
   if (nb <= 0) return PERM_ECUDA;
-  int grid_full = df.sms * nb;
-  int c = plan_chunk_exponent(n, g_end - g_begin, grid_full * kWarps);
-  uint64_t k_begin = g_begin >> c;
-  uint64_t k_end = (g_end + (1ull << c) - 1) >> c;
-  uint64_t nchunks = g_end > g_begin ? k_end - k_begin : 0;
+  const int grid_full = df.sms * nb;
+  L.c = plan_chunk_exponent(n, g_end - g_begin, grid_full * kWarps);
+  L.k_begin = g_begin >> L.c;
+  const uint64_t k_end = (g_end + (1ull << L.c) - 1) >> L.c;
+  L.nchunks = g_end > g_begin ? k_end - L.k_begin : 0;
   const uint64_t cpw = (uint64_t)(ke.chunks_per_warp > 0 ? ke.chunks_per_warp : 32);
-  uint64_t groups = (nchunks + cpw - 1) / cpw;
-  uint64_t need = (groups + kWarps - 1) / kWarps;
-  int grid = (int)(need < (uint64_t)grid_full ? (need > 0 ? need : 1) : grid_full);
+  const uint64_t groups = (L.nchunks + cpw - 1) / cpw;
+  const uint64_t need = (groups + kWarps - 1) / kWarps;
+  L.grid = (int)(need < (uint64_t)grid_full ? (need > 0 ? need : 1) : grid_full);
+  return PERM_OK;
+}
+
+// One Ryser launch over [g_begin, g_end): scratch from the stream-ordered
+// allocator, arrival counter zeroed, kernel, scratch released.
+static int launch_ryser(const KernelEntry& ke, const void* A, int n, uint64_t g_begin, uint64_t g_end, int mode,
+                        void* out, int32_t* status, cudaStream_t s, size_t part_bytes) {
+  RyserLaunch L;
+  int rc = plan_ryser_launch(ke, n, g_begin, g_end, L);
+  if (rc) return rc;
+  const int grid = L.grid, c = L.c;
+  const uint64_t k_begin = L.k_begin, nchunks = L.nchunks;
 
   size_t bytes = part_bytes * (size_t)grid + 16;
   void* ws = nullptr;
@@ -133,6 +145,7 @@ static int launch_ryser(const KernelEntry& ke, const void* A, int n, uint64_t g_
   args.status = status;
   args.abort_word = current_abort_word();
   args.aborted = counter + 1;
+  args.budget_ns = current_time_budget();
   void* params[] = {&args};
   cudaError_t e = cudaLaunchKernel(ke.fn, dim3(grid), dim3(kBlock), params, ke.smem, s);
   cudaError_t f = cudaFreeAsync(ws, s);
@@ -241,6 +254,11 @@ int perm_set_abort_word(volatile uint32_t* host_mapped) {
   return PERM_OK;
 }
 
+int perm_set_time_budget(uint64_t nanoseconds) {
+  g_budget_ns.store(nanoseconds, std::memory_order_release);
+  return PERM_OK;
+}
+
 int perm_abort_word_alloc(volatile uint32_t** host_word) {
   if (!host_word) return PERM_EINVAL;
   void* p = nullptr;
@@ -273,6 +291,7 @@ const char* perm_status_string(int status) {
     case PERM_ECUDA: return "PERM_ECUDA: a CUDA call failed";
     case PERM_ENOMEM: return "PERM_ENOMEM: scratch allocation failed";
     case PERM_EABORTED: return "PERM_EABORTED: stopped by the registered abort word";
+    case PERM_ETIMEOUT: return "PERM_ETIMEOUT: stopped when the time budget ran out";
     default: return "unknown perm status";
   }
 }

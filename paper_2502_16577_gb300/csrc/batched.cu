@@ -102,6 +102,9 @@ struct BatchArgs {
   unsigned int* counter;
   double* out;            // (re, im) per matrix
   int32_t* status;        // per matrix (optional)
+  const volatile uint32_t* abort_word;  // perm_set_abort_word (device view), or null
+  unsigned int* stopped;  // bit 0: aborted, bit 1: out of time (zeroed before the launch)
+  uint64_t budget_ns;     // perm_set_time_budget, 0: none
   int nmats;              // output matrices
   int nunits;
   int nitems;
@@ -557,7 +560,11 @@ __device__ __forceinline__ void batch_item(const BatchArgs& a, const BatchItem& 
 template <bool REAL>
 __global__ void __launch_bounds__(kBlock, 2) batch_main_kernel(BatchArgs a) {
   const int lane = threadIdx.x & 31;
+  const uint64_t t_start = global_ns();
   for (;;) {
+    // cancellation and the time budget, between work items (items left in the
+    // queue stay undone; the finish kernel then marks every matrix)
+    if (should_stop(a.abort_word, a.budget_ns, t_start, a.stopped)) break;
     int idx = 0;
     if (lane == 0) idx = (int)atomicAdd(a.counter, 1u);
     idx = __shfl_sync(0xffffffffu, idx, 0);
@@ -615,6 +622,7 @@ __global__ void batch_finish_kernel(BatchArgs a) {
   int32_t st = PERM_OK;
   if (bm.flags & 1) st = PERM_EINVAL;
   else if (bm.flags & 4) st = PERM_ERANGE;
+  else if (*a.stopped) st = stop_status(*a.stopped);
   if (a.type == PERM_F64) {
     a.out[m] = st != PERM_OK ? nan : (bm.flags & 2) ? 0.0 : (r.hi + r.lo) * f;
   } else if (st != PERM_OK) {
@@ -667,6 +675,11 @@ struct perm_batch_plan {
   int32_t* status = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;
+  // the graph's kernel nodes and the arguments they were last given: a replay
+  // with other buffers (or a new abort word / time budget) updates them in
+  // place, without a new capture or any allocation
+  std::vector<cudaGraphNode_t> knodes;
+  BatchArgs bound_args;
 };
 
 static void batch_free(perm_batch_plan* p) {
@@ -979,7 +992,7 @@ static int batch_build(perm_batch_plan* p) {
     cudaGetLastError();
     return PERM_ENOMEM;
   }
-  if (!p->d_counter && cudaMalloc(&p->d_counter, sizeof(unsigned int)) != cudaSuccess) {
+  if (!p->d_counter && cudaMalloc(&p->d_counter, 2 * sizeof(unsigned int)) != cudaSuccess) {
     cudaGetLastError();
     return PERM_ENOMEM;
   }
@@ -1011,6 +1024,9 @@ static BatchArgs batch_args(const perm_batch_plan* p) {
   a.counter = p->d_counter;
   a.out = p->out;
   a.status = p->status;
+  a.abort_word = current_abort_word();
+  a.stopped = p->d_counter + 1;
+  a.budget_ns = current_time_budget();
   a.nmats = p->count;
   a.nunits = p->nunits;
   a.nitems = p->nitems;
@@ -1021,7 +1037,7 @@ static BatchArgs batch_args(const perm_batch_plan* p) {
 // The execution sequence (captured into the plan's graph).
 static int batch_enqueue(const perm_batch_plan* p, cudaStream_t s) {
   BatchArgs a = batch_args(p);
-  if (cudaMemsetAsync(p->d_counter, 0, sizeof(unsigned int), s) != cudaSuccess) return PERM_ECUDA;
+  if (cudaMemsetAsync(p->d_counter, 0, 2 * sizeof(unsigned int), s) != cudaSuccess) return PERM_ECUDA;
   batch_prep_kernel<<<p->nunits, kBlock, 0, s>>>(a);
   int nb = 0;
   const bool real = p->type == PERM_F64;
@@ -1053,8 +1069,45 @@ static int batch_capture(perm_batch_plan* p) {
   if (!rc && cudaGraphInstantiate(&p->exec, g, 0) != cudaSuccess) rc = PERM_ECUDA;
   p->graph = g;
   cudaStreamDestroy(cs);
+  p->knodes.clear();
+  if (!rc) {
+    size_t num = 0;
+    if (cudaGraphGetNodes(g, nullptr, &num) != cudaSuccess) rc = PERM_ECUDA;
+    std::vector<cudaGraphNode_t> nodes(num);
+    if (!rc && num && cudaGraphGetNodes(g, nodes.data(), &num) != cudaSuccess) rc = PERM_ECUDA;
+    for (size_t i = 0; i < num && !rc; ++i) {
+      cudaGraphNodeType t;
+      if (cudaGraphNodeGetType(nodes[i], &t) != cudaSuccess) rc = PERM_ECUDA;
+      else if (t == cudaGraphNodeTypeKernel) p->knodes.push_back(nodes[i]);
+    }
+    p->bound_args = batch_args(p);
+  }
   if (rc) cudaGetLastError();
   return rc;
+}
+
+static bool same_args(const BatchArgs& x, const BatchArgs& y) {
+  return x.A == y.A && x.out == y.out && x.status == y.status && x.abort_word == y.abort_word &&
+         x.budget_ns == y.budget_ns;
+}
+
+// Point the instantiated graph's kernels at new buffers (every kernel of the
+// plan takes the one BatchArgs block).  No allocation, no capture.
+static int batch_rebind(perm_batch_plan* p, const BatchArgs& a) {
+  for (cudaGraphNode_t nd : p->knodes) {
+    cudaKernelNodeParams kp;
+    if (cudaGraphKernelNodeGetParams(nd, &kp) != cudaSuccess) return PERM_ECUDA;
+    BatchArgs arg = a;
+    void* params[] = {&arg};
+    kp.kernelParams = params;
+    kp.extra = nullptr;
+    if (cudaGraphExecKernelNodeSetParams(p->exec, nd, &kp) != cudaSuccess) {
+      cudaGetLastError();
+      return PERM_ECUDA;
+    }
+  }
+  p->bound_args = a;
+  return PERM_OK;
 }
 
 static int batch_create(perm_batch_plan** plan, int type, const int* ns_host, int count, const void* A_packed,
@@ -1143,8 +1196,16 @@ extern "C" int perm_batched_units(int k, const int32_t* labels, int max_units, i
   return (int)ups.size();
 }
 
-extern "C" int perm_batched(perm_batch_plan* plan, void* stream) {
+extern "C" int perm_batched(perm_batch_plan* plan, const void* A_packed, void* out, int32_t* status, void* stream) {
   if (!plan || !plan->exec) return PERM_EINVAL;
+  BatchArgs a = batch_args(plan);
+  if (A_packed) a.A = static_cast<const double*>(A_packed);
+  if (out) a.out = static_cast<double*>(out);
+  if (status) a.status = status;
+  if (!same_args(a, plan->bound_args)) {
+    int rc = batch_rebind(plan, a);
+    if (rc) return rc;
+  }
   return cudaGraphLaunch(plan->exec, static_cast<cudaStream_t>(stream)) == cudaSuccess ? PERM_OK : PERM_ECUDA;
 }
 

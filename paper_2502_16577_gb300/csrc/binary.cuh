@@ -175,13 +175,14 @@ __global__ void __launch_bounds__(kBlock, 2) ryser_bin_kernel(RyserArgs a) {
 #pragma unroll
   for (int k = 0; k < L; ++k) acc[k] = 0u;
   const int lane = threadIdx.x & 31;
+  const uint64_t t_start = global_ns();
   const uint64_t warp_id = (uint64_t)(blockIdx.x * kBlock + threadIdx.x) >> 5;
   const uint64_t nwarps = (uint64_t)(gridDim.x * kBlock) >> 5;
   const uint64_t ngroups = skip ? 0 : (a.nchunks + 31) / 32;
   const uint32_t nsteps = 1u << a.c;
 
   for (uint64_t q = warp_id; q < ngroups; q += nwarps) {
-    if (should_abort(a.abort_word, a.aborted)) break;
+    if (should_stop(a.abort_word, a.budget_ns, t_start, a.aborted)) break;
     const uint64_t kk = q * 32 + lane;
     const bool active = kk < a.nchunks;
     const uint64_t k = a.k_begin + kk;
@@ -263,7 +264,7 @@ __global__ void __launch_bounds__(kBlock, 2) ryser_bin_kernel(RyserArgs a) {
     int32_t st = PERM_OK;
     const bool aborted = *a.aborted != 0u;
     if (sh.bad_entry) st = PERM_EINVAL;
-    else if (aborted) st = PERM_EABORTED;
+    else if (aborted) st = stop_status(*a.aborted);
     else if (!sh.zero_row && sh.bound_log2 >= (float)(32 * L - N + 1) - 0.01f) st = PERM_EOVERFLOW;
     uint64_t* out = static_cast<uint64_t*>(a.out);
     if (a.mode == 1) {

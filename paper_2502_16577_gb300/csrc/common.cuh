@@ -96,19 +96,38 @@ struct RyserArgs {
   int32_t* status;    // optional device status word
   const volatile uint32_t* abort_word;  // device view of a host-mapped word, or null
   unsigned int* aborted;                // scratch word next to the counter (zeroed)
+  uint64_t budget_ns;                   // time budget of the sweep (perm_set_time_budget), 0: none
 };
 
-// Cancellation between chunk groups (perm_set_abort_word): lane 0 reads the
-// host-mapped word once per group and the warp follows it; a warp that stops
-// marks the launch so that the last CTA reports PERM_EABORTED.  No waiting.
-__device__ __forceinline__ bool should_abort(const volatile uint32_t* word, unsigned int* flag) {
-  if (!word) return false;
+// Nanoseconds of the GPU's global timer.
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Cancellation and the time budget, checked between chunk groups: lane 0 reads
+// the host-mapped abort word (perm_set_abort_word) and the time since t0 (the
+// warp's start) once per group, and the warp follows it.  A warp that stops
+// marks the launch (bit 0: aborted, bit 1: out of time) so that the finishing
+// CTA reports PERM_EABORTED or PERM_ETIMEOUT.  Nothing waits.
+__device__ __forceinline__ bool should_stop(const volatile uint32_t* word, uint64_t budget_ns, uint64_t t0,
+                                            unsigned int* flag) {
+  if (!word && !budget_ns) return false;
   uint32_t v = 0u;
-  if ((threadIdx.x & 31) == 0) v = *word;
+  if ((threadIdx.x & 31) == 0) {
+    if (word && *word != 0u) v = 1u;
+    else if (budget_ns && global_ns() - t0 > budget_ns) v = 2u;
+  }
   v = __shfl_sync(0xffffffffu, v, 0);
   if (v == 0u) return false;
-  if ((threadIdx.x & 31) == 0) atomicOr(flag, 1u);
+  if ((threadIdx.x & 31) == 0) atomicOr(flag, v);
   return true;
+}
+
+// The status of a stopped launch from its flag word (0 if it ran to the end).
+__device__ __forceinline__ int32_t stop_status(unsigned int flag) {
+  return (flag & 1u) ? PERM_EABORTED : (flag & 2u) ? PERM_ETIMEOUT : PERM_OK;
 }
 
 // Gray code of step g (Sec. 2): bit j set <=> column j is in the subset.

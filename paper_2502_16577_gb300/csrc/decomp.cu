@@ -480,7 +480,7 @@ int perm_decomp_eval(perm_decomp* p, double* out, void* stream) {
                                                     dd_bout, di_bst, blab.data())
                  : perm_batched_plan_create(&plan, PERM_F64, bks.data(), (int)nbat, dd_bat, boff.data(), dd_bout,
                                             di_bst);
-    if (rc == PERM_OK) rc = perm_batched(plan, stream);
+    if (rc == PERM_OK) rc = perm_batched(plan, nullptr, nullptr, nullptr, stream);
   }
   for (size_t l = 0; l < L && rc == PERM_OK; ++l) {
     const Mat& m = d.leaves[l].m;

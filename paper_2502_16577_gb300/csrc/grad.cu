@@ -37,10 +37,12 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 #include <vector>
 
 #include "common.cuh"
+#include "kernels.h"
 #include "real.cuh"
 
 namespace permgpu {
@@ -62,6 +64,9 @@ struct GradArgs {
   uint32_t sb;        // slots per matrix
   double* slots;      // [count][sb][n][8R] scalars, zeroed before the launch
   uint32_t* flags;    // [count]: bit 0 nonfinite, bit 1 range, 8..15 #zero rows, 16..23 first zero row
+  const volatile uint32_t* abort_word;  // perm_set_abort_word (device view), or null
+  uint64_t budget_ns;                   // perm_set_time_budget, 0: none
+  uint32_t* stopped;                    // bit 0: aborted, bit 1: out of time (zeroed)
 };
 
 // ------------------------------------------------------------ real values
@@ -354,7 +359,24 @@ __global__ void __launch_bounds__(kGThreads, (CPLX && R == 4) ? 2 : 4) ryser_gra
 
   uint64_t staged = ~0ull;
   int eoff[R];
+  __shared__ uint32_t s_stop[2];  // alternating, so a slot is rewritten only after a barrier
+  uint32_t iter = 0;
+  const uint64_t t_start = global_ns();
+  const bool watch = a.abort_word || a.budget_ns;
   for (uint64_t bi = blockIdx.x; bi < a.nbi; bi += gridDim.x) {
+    if (watch) {
+      // cancellation and the time budget between block-items, one decision per CTA
+      if (tid == 0) {
+        uint32_t v = 0u;
+        if (a.abort_word && *a.abort_word != 0u) v = 1u;
+        else if (a.budget_ns && global_ns() - t_start > a.budget_ns) v = 2u;
+        if (v) atomicOr(a.stopped, v);
+        s_stop[iter & 1u] = v;
+      }
+      __syncthreads();
+      if (s_stop[iter & 1u]) break;
+      ++iter;
+    }
     const uint64_t p = bi / a.bipm;
     const uint32_t q = (uint32_t)(bi - p * a.bipm);
     if (p != staged) {
@@ -516,7 +538,7 @@ struct FinishArgs {
   const uint32_t* flags;
   double* G;
   double* out;
-  uint32_t* status_bits;
+  uint32_t* status_bits;  // [0]: EINVAL / ERANGE bits, [1]: the sweep's stop bits
 };
 
 // G for column j of matrix p (grid: count x n, 256 threads): warp w sums slots
@@ -563,7 +585,7 @@ __global__ void __launch_bounds__(256) grad_finish_kernel(FinishArgs f) {
       const dd d = dd_add(dd{2.0 * U.hi, 2.0 * U.lo}, dd{-T.hi, -T.lo});
       g = sg * (d.hi + d.lo);
     }
-    if (fl & 3u) g = nan;
+    if ((fl & 3u) || f.status_bits[1]) g = nan;
     else if (zc >= 2 || (zc == 1 && lane != zi)) g = 0.0;
     f.G[((size_t)p * n * n + (size_t)lane * n + j) * W + c] = g;
   }
@@ -600,7 +622,7 @@ __global__ void __launch_bounds__(256) grad_perm_kernel(FinishArgs f) {
   const uint32_t fl = f.flags[p];
   const double nan = __longlong_as_double(0x7ff8000000000000ll);
   double vr = re.hi + re.lo, vi = im.hi + im.lo;
-  if (fl & 3u) vr = vi = nan;
+  if ((fl & 3u) || f.status_bits[1]) vr = vi = nan;
   else if ((fl >> 8) & 0xFF) vr = vi = 0.0;
   f.out[p * W] = vr;
   if (CPLX) f.out[p * W + 1] = vi;
@@ -608,8 +630,8 @@ __global__ void __launch_bounds__(256) grad_perm_kernel(FinishArgs f) {
 }
 
 __global__ void grad_status_kernel(const uint32_t* bits, int32_t* status) {
-  const uint32_t b = *bits;
-  if (status) *status = (b & 1u) ? PERM_EINVAL : (b & 2u) ? PERM_ERANGE : PERM_OK;
+  const uint32_t b = bits[0];
+  if (status) *status = (b & 1u) ? PERM_EINVAL : (b & 2u) ? PERM_ERANGE : stop_status(bits[1]);
 }
 
 // n = 0: the empty product (perm = 1, no gradient entries).
@@ -716,40 +738,41 @@ int device_prepare(int dev) {
 
 using namespace permgpu;
 
-extern "C" int perm_grad_batched(const void* A, int n, int count, int type, void* out, void* G, int32_t* status,
-                                 void* stream) {
-  if (type != PERM_F64 && type != PERM_C128) return PERM_EINVAL;
-  if (n < 0 || n > 32) return PERM_ERANGE;
-  if (count < 0) return PERM_EINVAL;
-  if (count == 0) return status ? (cudaMemsetAsync(status, 0, sizeof(int32_t), (cudaStream_t)stream) == cudaSuccess
-                                       ? PERM_OK
-                                       : PERM_ECUDA)
-                                : PERM_OK;
-  if (!out || (n > 0 && (!A || !G))) return PERM_EINVAL;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const bool cplx = type == PERM_C128;
-  const int W = cplx ? 2 : 1;
-  if (n == 0) {
-    grad_empty_kernel<<<(count + 255) / 256, 256, 0, s>>>(static_cast<double*>(out), count, W, status);
-    return cudaGetLastError() == cudaSuccess ? PERM_OK : PERM_ECUDA;
-  }
+namespace permgpu {
+namespace {
+
+// Launch shape and workspace of one equal-order gradient sweep.
+struct GradCfg {
+  int n = 0, count = 0, R = 1, cq = 0, grid = 0;
+  bool cplx = false;
+  uint32_t qc = 0, bipm = 0, sb = 0;
+  uint64_t nbi = 0;
+  size_t smem = 0, slot_doubles = 0, ws_bytes = 0;
+  KernelFn fn = nullptr;
+};
+
+// n >= 1, count >= 1.
+int grad_configure(int n, int count, bool cplx, GradCfg& g) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return PERM_ECUDA;
   const int sms = device_prepare(dev);
   if (sms <= 0) return PERM_ECUDA;
-  const int R = n <= 8 ? 1 : n <= 16 ? 2 : n <= 24 ? 3 : 4;
-  const int NR = kGL * R;
-  KernelFn fn = grad_kernel(cplx, R);
-
+  const int W = cplx ? 2 : 1;
+  g.n = n;
+  g.count = count;
+  g.cplx = cplx;
+  g.R = n <= 8 ? 1 : n <= 16 ? 2 : n <= 24 ? 3 : 4;
+  const int NR = kGL * g.R;
+  g.fn = grad_kernel(cplx, g.R);
   // chunk length: the largest cq <= 9 that keeps 4 CTAs (cplx R=4: 2) per SM
   // resident, then shortened so that small batches still fill the GPU
   int cq_max = 0, ctas = 0;
   {
-    const int want = (cplx && R == 4) ? 2 : 4;
+    const int want = (cplx && g.R == 4) ? 2 : 4;
     for (int c = 9; c >= 0; --c) {
-      const size_t sm = grad_smem(cplx, n, R, c);
+      const size_t sm = grad_smem(cplx, n, g.R, c);
       int nb = 0;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kGThreads, sm) != cudaSuccess) {
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, g.fn, kGThreads, sm) != cudaSuccess) {
         cudaGetLastError();
         return PERM_ECUDA;
       }
@@ -767,62 +790,67 @@ extern "C" int perm_grad_batched(const void* A, int n, int count, int type, void
   cq = cq < 4 ? 4 : cq;
   cq = cq > cq_max ? cq_max : cq;
   if (cq > n - 5) cq = n - 5 > 0 ? n - 5 : 0;
-  const uint32_t qc = 1u << (n - 1 - cq);
-  const uint32_t bipm = qc >= 16 ? qc / 16 : 1;
-  const uint64_t nbi = (uint64_t)count * bipm;
-  const int grid = (int)(nbi < B_full ? nbi : B_full);
-  const uint32_t sb = bipm < (uint32_t)grid ? bipm : (uint32_t)grid;
-  const size_t slot_doubles = (size_t)count * sb * n * NR * W;
-  const size_t bytes = sizeof(double) * slot_doubles + sizeof(uint32_t) * ((size_t)count + 4);
-  void* ws = nullptr;
-  if (cudaMallocAsync(&ws, bytes, s) != cudaSuccess) {
-    cudaGetLastError();
-    return PERM_ENOMEM;
-  }
+  g.cq = cq;
+  g.qc = 1u << (n - 1 - cq);
+  g.bipm = g.qc >= 16 ? g.qc / 16 : 1;
+  g.nbi = (uint64_t)count * g.bipm;
+  g.grid = (int)(g.nbi < B_full ? g.nbi : B_full);
+  g.sb = g.bipm < (uint32_t)g.grid ? g.bipm : (uint32_t)g.grid;
+  g.slot_doubles = (size_t)count * g.sb * n * NR * W;
+  g.ws_bytes = sizeof(double) * g.slot_doubles + sizeof(uint32_t) * ((size_t)count + 4);
+  g.smem = grad_smem(cplx, n, g.R, cq);
+  return PERM_OK;
+}
+
+// The sweep and its finishing kernels on a caller-provided workspace of
+// g.ws_bytes (cleared here, on the stream).  Allocates nothing.
+int grad_launch(const GradCfg& g, const void* A, void* out, void* G, int32_t* status, void* ws, cudaStream_t s) {
   double* slots = static_cast<double*>(ws);
-  uint32_t* flags = reinterpret_cast<uint32_t*>(slots + slot_doubles);
-  uint32_t* bits = flags + count;
-  if (cudaMemsetAsync(ws, 0, bytes, s) != cudaSuccess) {
-    cudaFreeAsync(ws, s);
+  uint32_t* flags = reinterpret_cast<uint32_t*>(slots + g.slot_doubles);
+  uint32_t* bits = flags + g.count;
+  if (cudaMemsetAsync(ws, 0, g.ws_bytes, s) != cudaSuccess) {
     cudaGetLastError();
     return PERM_ECUDA;
   }
   GradArgs ga;
   memset(&ga, 0, sizeof(ga));
   ga.A = static_cast<const double*>(A);
-  ga.n = n;
-  ga.cq = cq;
-  ga.qc = qc;
-  ga.bipm = bipm;
-  ga.nbi = nbi;
-  ga.sb = sb;
+  ga.n = g.n;
+  ga.cq = g.cq;
+  ga.qc = g.qc;
+  ga.bipm = g.bipm;
+  ga.nbi = g.nbi;
+  ga.sb = g.sb;
   ga.slots = slots;
   ga.flags = flags;
-  const size_t smem = grad_smem(cplx, n, R, cq);
+  ga.abort_word = current_abort_word();
+  ga.budget_ns = current_time_budget();
+  ga.stopped = bits + 1;
   void* params[] = {&ga};
-  cudaError_t e = cudaLaunchKernel(reinterpret_cast<const void*>(fn), dim3(grid), dim3(kGThreads), params, smem, s);
+  cudaError_t e =
+      cudaLaunchKernel(reinterpret_cast<const void*>(g.fn), dim3(g.grid), dim3(kGThreads), params, g.smem, s);
   FinishArgs fa;
   memset(&fa, 0, sizeof(fa));
   fa.A = static_cast<const double*>(A);
-  fa.n = n;
-  fa.NR = NR;
-  fa.count = count;
-  fa.sb = sb;
+  fa.n = g.n;
+  fa.NR = kGL * g.R;
+  fa.count = g.count;
+  fa.sb = g.sb;
   fa.slots = slots;
   fa.flags = flags;
   fa.G = static_cast<double*>(G);
   fa.out = static_cast<double*>(out);
   fa.status_bits = bits;
   if (e == cudaSuccess) {
-    if (cplx)
-      grad_finish_kernel<true><<<dim3(count, n), 256, 0, s>>>(fa);
+    if (g.cplx)
+      grad_finish_kernel<true><<<dim3(g.count, g.n), 256, 0, s>>>(fa);
     else
-      grad_finish_kernel<false><<<dim3(count, n), 256, 0, s>>>(fa);
+      grad_finish_kernel<false><<<dim3(g.count, g.n), 256, 0, s>>>(fa);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) {
-    const unsigned pb = (unsigned)((count + 7) / 8);
-    if (cplx)
+    const unsigned pb = (unsigned)((g.count + 7) / 8);
+    if (g.cplx)
       grad_perm_kernel<true><<<pb, 256, 0, s>>>(fa);
     else
       grad_perm_kernel<false><<<pb, 256, 0, s>>>(fa);
@@ -832,96 +860,201 @@ extern "C" int perm_grad_batched(const void* A, int n, int count, int type, void
     grad_status_kernel<<<1, 1, 0, s>>>(bits, status);
     e = cudaGetLastError();
   }
-  const cudaError_t fr = cudaFreeAsync(ws, s);
-  if (e != cudaSuccess || fr != cudaSuccess) {
+  if (e != cudaSuccess) {
     cudaGetLastError();
     return PERM_ECUDA;
   }
   return PERM_OK;
 }
 
+}  // namespace
+}  // namespace permgpu
+
+extern "C" int perm_grad_batched(const void* A, int n, int count, int type, void* out, void* G, int32_t* status,
+                                 void* stream) {
+  if (type != PERM_F64 && type != PERM_C128) return PERM_EINVAL;
+  if (n < 0 || n > 32) return PERM_ERANGE;
+  if (count < 0) return PERM_EINVAL;
+  if (count == 0) return status ? (cudaMemsetAsync(status, 0, sizeof(int32_t), (cudaStream_t)stream) == cudaSuccess
+                                       ? PERM_OK
+                                       : PERM_ECUDA)
+                                : PERM_OK;
+  if (!out || (n > 0 && (!A || !G))) return PERM_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bool cplx = type == PERM_C128;
+  const int W = cplx ? 2 : 1;
+  if (n == 0) {
+    grad_empty_kernel<<<(count + 255) / 256, 256, 0, s>>>(static_cast<double*>(out), count, W, status);
+    return cudaGetLastError() == cudaSuccess ? PERM_OK : PERM_ECUDA;
+  }
+  GradCfg g;
+  int rc = grad_configure(n, count, cplx, g);
+  if (rc) return rc;
+  void* ws = nullptr;
+  if (cudaMallocAsync(&ws, g.ws_bytes, s) != cudaSuccess) {
+    cudaGetLastError();
+    return PERM_ENOMEM;
+  }
+  rc = grad_launch(g, A, out, G, status, ws, s);
+  if (cudaFreeAsync(ws, s) != cudaSuccess && rc == PERM_OK) rc = PERM_ECUDA;
+  if (rc) cudaGetLastError();
+  return rc;
+}
+
 extern "C" int perm_grad(const void* A, int n, int type, void* out, void* G, int32_t* status, void* stream) {
   return perm_grad_batched(A, n, 1, type, out, G, status, stream);
 }
+
+// A mixed-order gradient plan: the matrices grouped by order, each group
+// gathered into a contiguous batch, swept by one equal-order launch and
+// scattered back.  Every device buffer is allocated once, at creation.
+struct perm_grad_plan {
+  struct Group {
+    int n = 0, cnt = 0;
+    GradCfg cfg;
+    double* Ag = nullptr;  // gathered matrices, then G, then out
+    double* Gg = nullptr;
+    double* og = nullptr;
+    int64_t* offs = nullptr;  // element offsets in A_packed / G_packed (scalars x W)
+    int64_t* oidx = nullptr;  // output index of every matrix
+  };
+  int type = PERM_F64;
+  int count = 0;
+  std::vector<Group> groups;
+  void* buf = nullptr;   // one allocation: group buffers, index arrays, statuses
+  void* ws = nullptr;    // sweep workspace, shared by the groups (stream-ordered)
+  int32_t* gst = nullptr;
+};
+
+static void grad_plan_free(perm_grad_plan* p) {
+  if (!p) return;
+  cudaFree(p->buf);
+  cudaFree(p->ws);
+  delete p;
+}
+
+extern "C" int perm_grad_plan_create(perm_grad_plan** plan, int type, const int* ns_host, int count,
+                                     const int64_t* offsets_host) {
+  if (!plan) return PERM_EINVAL;
+  *plan = nullptr;
+  if (type != PERM_F64 && type != PERM_C128) return PERM_EINVAL;
+  if (count < 0 || (count > 0 && (!ns_host || !offsets_host))) return PERM_EINVAL;
+  const int W = type == PERM_C128 ? 2 : 1;
+  std::vector<std::vector<int>> members(33);
+  for (int m = 0; m < count; ++m) {
+    const int n = ns_host[m];
+    if (n < 0 || n > 32) return PERM_ERANGE;
+    if (offsets_host[m] < 0) return PERM_EINVAL;
+    members[n].push_back(m);
+  }
+  perm_grad_plan* p = new perm_grad_plan();
+  p->type = type;
+  p->count = count;
+  size_t doubles = 0, words = 0, ws_max = 0;
+  for (int n = 0; n <= 32; ++n) {
+    if (members[n].empty()) continue;
+    perm_grad_plan::Group g;
+    g.n = n;
+    g.cnt = (int)members[n].size();
+    if (n > 0) {
+      int rc = grad_configure(n, g.cnt, type == PERM_C128, g.cfg);
+      if (rc) {
+        grad_plan_free(p);
+        return rc;
+      }
+      ws_max = std::max(ws_max, g.cfg.ws_bytes);
+    }
+    doubles += (size_t)g.cnt * ((size_t)n * n * W * 2 + W);
+    words += 2 * (size_t)g.cnt;
+    p->groups.push_back(g);
+  }
+  const size_t bytes = sizeof(double) * doubles + sizeof(int64_t) * words + sizeof(int32_t) * (p->groups.size() + 1);
+  if (cudaMalloc(&p->buf, bytes) != cudaSuccess || (ws_max && cudaMalloc(&p->ws, ws_max) != cudaSuccess)) {
+    cudaGetLastError();
+    grad_plan_free(p);
+    return PERM_ENOMEM;
+  }
+  double* d = static_cast<double*>(p->buf);
+  int64_t* idx = reinterpret_cast<int64_t*>(d + doubles);
+  p->gst = reinterpret_cast<int32_t*>(idx + words);
+  std::vector<int64_t> hidx(words);
+  size_t ioff = 0;
+  for (perm_grad_plan::Group& g : p->groups) {
+    const size_t nn_w = (size_t)g.n * g.n * W;
+    g.Ag = d;
+    g.Gg = d + (size_t)g.cnt * nn_w;
+    g.og = g.Gg + (size_t)g.cnt * nn_w;
+    d = g.og + (size_t)g.cnt * W;
+    g.offs = idx + ioff;
+    g.oidx = g.offs + g.cnt;
+    const std::vector<int>& ms = members[g.n];
+    for (int k = 0; k < g.cnt; ++k) {
+      hidx[ioff + k] = offsets_host[ms[k]] * W;
+      hidx[ioff + g.cnt + k] = ms[k];
+    }
+    ioff += 2 * (size_t)g.cnt;
+  }
+  if (words && cudaMemcpy(idx, hidx.data(), sizeof(int64_t) * words, cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaGetLastError();
+    grad_plan_free(p);
+    return PERM_ECUDA;
+  }
+  *plan = p;
+  return PERM_OK;
+}
+
+extern "C" int perm_grad_plan_run(perm_grad_plan* p, const void* A_packed, void* out, void* G_packed,
+                                  int32_t* status, void* stream) {
+  if (!p) return PERM_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (p->count == 0)
+    return status ? (cudaMemsetAsync(status, 0, sizeof(int32_t), s) == cudaSuccess ? PERM_OK : PERM_ECUDA)
+                  : PERM_OK;
+  if (!out) return PERM_EINVAL;
+  const int W = p->type == PERM_C128 ? 2 : 1;
+  int rc = PERM_OK;
+  for (size_t gi = 0; gi < p->groups.size() && rc == PERM_OK; ++gi) {
+    const perm_grad_plan::Group& g = p->groups[gi];
+    const int nn_w = g.n * g.n * W;
+    if (g.n > 0 && (!A_packed || !G_packed)) return PERM_EINVAL;
+    if (g.n > 0) {
+      grad_gather_kernel<<<g.cnt, 128, 0, s>>>(static_cast<const double*>(A_packed), g.offs, nn_w, g.Ag);
+      if (cudaGetLastError() != cudaSuccess) rc = PERM_ECUDA;
+      if (rc == PERM_OK) rc = grad_launch(g.cfg, g.Ag, g.og, g.Gg, p->gst + gi, p->ws, s);
+    } else {
+      grad_empty_kernel<<<(g.cnt + 255) / 256, 256, 0, s>>>(g.og, g.cnt, W, p->gst + gi);
+      if (cudaGetLastError() != cudaSuccess) rc = PERM_ECUDA;
+    }
+    if (rc == PERM_OK) {
+      grad_scatter_kernel<<<g.cnt, 128, 0, s>>>(g.Gg, g.og, g.offs, g.oidx, nn_w, W, static_cast<double*>(G_packed),
+                                                static_cast<double*>(out));
+      if (cudaGetLastError() != cudaSuccess) rc = PERM_ECUDA;
+    }
+  }
+  if (rc == PERM_OK) {
+    grad_status_merge_kernel<<<1, 1, 0, s>>>(p->gst, (int)p->groups.size(), status);
+    if (cudaGetLastError() != cudaSuccess) rc = PERM_ECUDA;
+  }
+  if (rc != PERM_OK) cudaGetLastError();
+  return rc;
+}
+
+extern "C" void perm_grad_plan_destroy(perm_grad_plan* plan) { grad_plan_free(plan); }
 
 extern "C" int perm_grad_batched_mixed(int type, const int* ns_host, int count, const void* A_packed,
                                        const int64_t* offsets_host, void* out, void* G_packed, int32_t* status,
                                        void* stream) {
   if (type != PERM_F64 && type != PERM_C128) return PERM_EINVAL;
   if (count < 0 || (count > 0 && (!ns_host || !offsets_host || !out))) return PERM_EINVAL;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const int W = type == PERM_C128 ? 2 : 1;
-  if (count == 0)
-    return status ? (cudaMemsetAsync(status, 0, sizeof(int32_t), s) == cudaSuccess ? PERM_OK : PERM_ECUDA)
-                  : PERM_OK;
-  // group the matrices by order
-  std::vector<std::vector<int>> groups(33);
-  for (int m = 0; m < count; ++m) {
-    const int n = ns_host[m];
-    if (n < 0 || n > 32) return PERM_ERANGE;
-    if (offsets_host[m] < 0) return PERM_EINVAL;
-    if (n > 0 && (!A_packed || !G_packed)) return PERM_EINVAL;
-    groups[n].push_back(m);
-  }
-  int ngroups = 0;
-  size_t tmp_doubles = 0, idx_words = 0;
-  for (int n = 0; n <= 32; ++n)
-    if (!groups[n].empty()) {
-      ++ngroups;
-      tmp_doubles += groups[n].size() * ((size_t)n * n * W * 2 + W);
-      idx_words += 2 * groups[n].size();
-    }
-  void* ws = nullptr;
-  const size_t bytes = sizeof(double) * tmp_doubles + sizeof(int64_t) * idx_words + sizeof(int32_t) * 40 + 64;
-  if (cudaMalloc(&ws, bytes) != cudaSuccess) {
-    cudaGetLastError();
-    return PERM_ENOMEM;
-  }
-  double* tmp = static_cast<double*>(ws);
-  int64_t* idx = reinterpret_cast<int64_t*>(tmp + tmp_doubles);
-  int32_t* gst = reinterpret_cast<int32_t*>(idx + idx_words);
-  std::vector<int64_t> hidx(idx_words);
-  int rc = PERM_OK, g = 0;
-  size_t toff = 0, ioff = 0;
-  for (int n = 0; n <= 32 && rc == PERM_OK; ++n) {
-    const std::vector<int>& ms = groups[n];
-    if (ms.empty()) continue;
-    const int cnt = (int)ms.size();
-    const int nn_w = n * n * W;
-    double* Ag = tmp + toff;
-    double* Gg = Ag + (size_t)cnt * nn_w;
-    double* og = Gg + (size_t)cnt * nn_w;
-    toff += (size_t)cnt * ((size_t)nn_w * 2 + W);
-    int64_t* offs = idx + ioff;
-    int64_t* oidx = offs + cnt;
-    for (int k = 0; k < cnt; ++k) {
-      hidx[ioff + k] = offsets_host[ms[k]] * W;
-      hidx[ioff + cnt + k] = ms[k];
-    }
-    // pageable source: the copy has completed when cudaMemcpyAsync returns
-    if (cudaMemcpyAsync(offs, hidx.data() + ioff, sizeof(int64_t) * 2 * cnt, cudaMemcpyHostToDevice, s) !=
-        cudaSuccess)
-      rc = PERM_ECUDA;
-    ioff += 2 * (size_t)cnt;
-    if (rc == PERM_OK && n > 0) {
-      grad_gather_kernel<<<cnt, 128, 0, s>>>(static_cast<const double*>(A_packed), offs, nn_w, Ag);
-      if (cudaGetLastError() != cudaSuccess) rc = PERM_ECUDA;
-    }
-    if (rc == PERM_OK) rc = perm_grad_batched(Ag, n, cnt, type, og, Gg, gst + g, stream);
-    if (rc == PERM_OK) {
-      grad_scatter_kernel<<<cnt, 128, 0, s>>>(Gg, og, offs, oidx, nn_w, W, static_cast<double*>(G_packed),
-                                              static_cast<double*>(out));
-      if (cudaGetLastError() != cudaSuccess) rc = PERM_ECUDA;
-    }
-    ++g;
-  }
-  if (rc == PERM_OK) {
-    grad_status_merge_kernel<<<1, 1, 0, s>>>(gst, ngroups, status);
-    if (cudaGetLastError() != cudaSuccess) rc = PERM_ECUDA;
-  }
-  // the workspace is released after the stream's work on it
-  if (cudaStreamSynchronize(s) != cudaSuccess && rc == PERM_OK) rc = PERM_ECUDA;
-  if (cudaFree(ws) != cudaSuccess && rc == PERM_OK) rc = PERM_ECUDA;
+  for (int m = 0; m < count; ++m)
+    if (ns_host[m] > 0 && (!A_packed || !G_packed)) return PERM_EINVAL;
+  perm_grad_plan* p = nullptr;
+  int rc = perm_grad_plan_create(&p, type, ns_host, count, offsets_host);
+  if (rc) return rc;
+  rc = perm_grad_plan_run(p, A_packed, out, G_packed, status, stream);
+  // the plan's buffers are released after the stream's work on them
+  if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess && rc == PERM_OK) rc = PERM_ECUDA;
+  grad_plan_free(p);
   if (rc != PERM_OK) cudaGetLastError();
   return rc;
 }

@@ -32,12 +32,11 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 
 struct NoAllocDevice {
   void* scratch = nullptr;  // device address of g_noalloc_scratch
-  int sms = 0;
 };
 
 // Per-device set-up, once, with that device current: the device address of
 // the scratch array (its host-side name is only a stand-in and must never be
-// passed to a kernel) and the SM count.
+// passed to a kernel).
 static int noalloc_device(NoAllocDevice& out) {
   static std::mutex mu;
   static NoAllocDevice cache[kNoAllocMaxDevices];
@@ -51,9 +50,6 @@ static int noalloc_device(NoAllocDevice& out) {
       cudaGetLastError();
       return PERM_ECUDA;
     }
-    int sms = 0;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return PERM_ECUDA;
-    d.sms = sms;
     d.scratch = ptr;
   }
   out = d;
@@ -84,18 +80,12 @@ extern "C" int perm_f64_noalloc(const double* A, int n, double* out, int32_t* st
   }
   KernelEntry ke = n <= 24 ? real_entry_lo(n) : n <= 44 ? real_entry_mid(n) : real_entry_hi(n);
   if (!ke.fn) return PERM_EINVAL;
-  if (ke.smem > 48 * 1024 &&
-      cudaFuncSetAttribute(ke.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ke.smem) != cudaSuccess)
-    return PERM_ECUDA;
-  int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, ke.fn, kBlock, ke.smem) != cudaSuccess || nb <= 0)
-    return PERM_ECUDA;
   const uint64_t N = 1ull << (n - 1);
-  const int grid_full = nd.sms * nb;
-  const int c = plan_chunk_exponent(n, N, grid_full * kWarps);
-  const uint64_t nchunks = N >> c;
-  const uint64_t need = ((nchunks + 31) / 32 + kWarps - 1) / kWarps;
-  const int grid = (int)(need < (uint64_t)grid_full ? (need > 0 ? need : 1) : grid_full);
+  RyserLaunch L;  // the launch shape of perm() for this matrix
+  rc = plan_ryser_launch(ke, n, 0, N, L);
+  if (rc) return rc;
+  const int grid = L.grid, c = L.c;
+  const uint64_t nchunks = L.nchunks;
   // the fixed array must hold one partial per CTA and the counter
   const size_t part_bytes = sizeof(dd) * (size_t)grid;
   if (part_bytes + 2 * sizeof(unsigned int) > kNoAllocScratchBytes) return PERM_ENOMEM;
@@ -118,6 +108,7 @@ extern "C" int perm_f64_noalloc(const double* A, int n, double* out, int32_t* st
   args.status = status;
   args.abort_word = current_abort_word();
   args.aborted = counter + 1;
+  args.budget_ns = current_time_budget();
   void* params[] = {&args};
   if (cudaLaunchKernel(ke.fn, dim3(grid), dim3(kBlock), params, ke.smem, s) != cudaSuccess) {
     cudaGetLastError();

@@ -3,6 +3,7 @@
 // runs 8 independent dependency chains per thread of one instruction kind on
 // every SM and is timed with CUDA events; the chains are written out so the
 // compiler keeps them.
+#include <math.h>
 #include <stdint.h>
 
 #include "common.cuh"
@@ -61,33 +62,32 @@ extern "C" int perm_pipe_peaks(double* out, int count, void* stream) {
     cudaGetLastError();
     return PERM_ENOMEM;
   }
-  cudaEvent_t e0, e1;
-  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return PERM_ECUDA;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = PERM_OK;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = PERM_ECUDA;
   void (*kernels[5])(unsigned long long*, uint32_t) = {peak_kernel<0>, peak_kernel<1>, peak_kernel<2>, peak_kernel<3>,
                                                        peak_kernel<4>};
-  int rc = PERM_OK;
   const double ops = (double)grid * block * kPeakIters * kPeakUnroll * kPeakChains;
-  for (int k = 0; k < 5 && k < count; ++k) {
+  for (int k = 0; k < count; ++k) out[k] = NAN;  // written only after a successful timing
+  for (int k = 0; k < 5 && k < count && rc == PERM_OK; ++k) {
     kernels[k]<<<grid, block, 0, s>>>(sink, 3u);  // warm-up
     float best = 1e30f;
     for (int rep = 0; rep < 3; ++rep) {
-      cudaEventRecord(e0, s);
-      kernels[k]<<<grid, block, 0, s>>>(sink, 3u + rep);
-      cudaEventRecord(e1, s);
-      if (cudaEventSynchronize(e1) != cudaSuccess) {
-        rc = PERM_ECUDA;
-        break;
-      }
       float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
+      if (cudaEventRecord(e0, s) != cudaSuccess) rc = PERM_ECUDA;
+      if (!rc) kernels[k]<<<grid, block, 0, s>>>(sink, 3u + rep);
+      if (!rc && cudaEventRecord(e1, s) != cudaSuccess) rc = PERM_ECUDA;
+      if (!rc && cudaEventSynchronize(e1) != cudaSuccess) rc = PERM_ECUDA;
+      if (!rc && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = PERM_ECUDA;
+      if (rc) break;
       if (ms < best) best = ms;
     }
-    out[k] = ops / (best * 1e-3);  // lane-instructions per second
+    if (!rc) out[k] = ops / (best * 1e-3);  // lane-instructions per second
   }
-  if (cudaGetLastError() != cudaSuccess) rc = PERM_ECUDA;
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  if (cudaGetLastError() != cudaSuccess && rc == PERM_OK) rc = PERM_ECUDA;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
   cudaFreeAsync(sink, s);
-  cudaStreamSynchronize(s);
+  if (cudaStreamSynchronize(s) != cudaSuccess && rc == PERM_OK) rc = PERM_ECUDA;
   return rc;
 }

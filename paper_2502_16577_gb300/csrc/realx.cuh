@@ -190,13 +190,14 @@ __global__ void __launch_bounds__(kBlock, (N <= 40 ? 2 : 1)) ryser_realx_kernel(
 
   dd acc = {0.0, 0.0};
   const int lane = threadIdx.x & 31;
+  const uint64_t t_start = global_ns();
   const uint64_t warp_id = (uint64_t)(blockIdx.x * kBlock + threadIdx.x) >> 5;
   const uint64_t nwarps = (uint64_t)(gridDim.x * kBlock) >> 5;
   const uint64_t ngroups = skip ? 0 : (a.nchunks + 31) / 32;
   const uint32_t nsteps = 1u << a.c;
 
   for (uint64_t q = warp_id; q < ngroups; q += nwarps) {
-    if (should_abort(a.abort_word, a.aborted)) break;
+    if (should_stop(a.abort_word, a.budget_ns, t_start, a.aborted)) break;
     const uint64_t kk = q * 32 + lane;
     const bool active = kk < a.nchunks;
     const uint64_t k = a.k_begin + kk;
@@ -264,7 +265,7 @@ __global__ void __launch_bounds__(kBlock, (N <= 40 ? 2 : 1)) ryser_realx_kernel(
       int32_t st = PERM_OK;
       if (sh.nonfinite) st = PERM_EINVAL;
       else if (sh.bound_log2 + N > 1000) st = PERM_ERANGE;
-      else if (*a.aborted) st = PERM_EABORTED;
+      else if (*a.aborted) st = stop_status(*a.aborted);
       const double nan = __longlong_as_double(0x7ff8000000000000ll);
       tot = dd_make(tot.hi, tot.lo);
       if (a.mode == 0) {

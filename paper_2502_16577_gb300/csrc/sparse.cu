@@ -50,13 +50,17 @@ struct SpArgs {
   int nnz;
   int c;
   int one;
-  uint64_t nchunks;
+  int mode;         // 0: write the finished permanent, 1: write the raw range sum (hi, lo)
+  int paper_order;  // 1: Alg. 2's own column order (no quiet-row reordering)
+  uint64_t g_begin, g_end;  // accumulated steps
+  uint64_t k_begin, nchunks;  // visited chunks [k_begin, k_begin + nchunks)
   dd* part;
   unsigned int* counter;
   double* out;
   int32_t* status;
   const volatile uint32_t* abort_word;
   unsigned int* aborted;
+  uint64_t budget_ns;
 };
 
 struct SpShared {
@@ -157,7 +161,7 @@ __global__ void __launch_bounds__(kSpBlock) ryser_sparse_kernel(SpArgs a) {
     for (int j = 0; j < 64; ++j) s_cmap[j] = j;
     int chosen[4] = {-1, -1, -1, -1};
     unsigned long long masks[5] = {0ull, 0ull, 0ull, 0ull, 0ull};
-    const int bmax = sh.bad ? 0 : min(min(a.c, 4), n - 1);
+    const int bmax = (sh.bad || a.paper_order) ? 0 : min(min(a.c, 4), n - 1);
     int B = 0;
     float best_cost = (float)n + 2.0f;
     for (int b = 0; b < bmax; ++b) {
@@ -210,6 +214,7 @@ __global__ void __launch_bounds__(kSpBlock) ryser_sparse_kernel(SpArgs a) {
   const int F0 = 33 * n + 1022 - 56 - sh.sum_s;
   const int tid = threadIdx.x;
   const int lane = tid & 31;
+  const uint64_t t_start = global_ns();
   const uint64_t warp_id = (uint64_t)(blockIdx.x * kSpBlock + tid) >> 5;
   const uint64_t nwarps = (uint64_t)(gridDim.x * kSpBlock) >> 5;
   const uint64_t ngroups = skip ? 0 : (a.nchunks + 31) / 32;
@@ -217,10 +222,21 @@ __global__ void __launch_bounds__(kSpBlock) ryser_sparse_kernel(SpArgs a) {
   dd acc = {0.0, 0.0};
 
   for (uint64_t q = warp_id; q < ngroups; q += nwarps) {
-    if (should_abort(a.abort_word, a.aborted)) break;
-    const uint64_t k = q * 32 + lane;
-    const bool active = k < a.nchunks;
+    if (should_stop(a.abort_word, a.budget_ns, t_start, a.aborted)) break;
+    const uint64_t kk = q * 32 + lane;
+    const bool active = kk < a.nchunks;
+    const uint64_t k = a.k_begin + kk;
     const uint64_t g0 = k << a.c;
+    // steps of this chunk inside [g_begin, g_end): local t in [tlo, tlo + tcnt)
+    uint32_t tlo, tcnt;
+    {
+      const uint64_t len = 1ull << a.c;
+      const uint64_t lo = a.g_begin > g0 ? a.g_begin - g0 : 0;
+      uint64_t hi = a.g_end > g0 ? a.g_end - g0 : 0;
+      if (hi > len) hi = len;
+      tlo = (uint32_t)lo;
+      tcnt = (active && hi > lo) ? (uint32_t)(hi - lo) : 0u;
+    }
     const uint32_t kb = (uint32_t)(k & 1u) << a.c;
     const uint32_t gpar = (uint32_t)(g0 & 1u);
     // x at Gray(g0) and its zero count
@@ -271,7 +287,7 @@ __global__ void __launch_bounds__(kSpBlock) ryser_sparse_kernel(SpArgs a) {
           eposq += prod_mul(pq, (uint32_t)aa, (uint32_t)(aa >> 32));
         }
       }
-      if (zeros == 0 && active) {
+      if (zeros == 0 && t - tlo < tcnt) {
         Prod pa, pb;
         prod_init(pa);
         prod_init(pb);
@@ -322,37 +338,34 @@ __global__ void __launch_bounds__(kSpBlock) ryser_sparse_kernel(SpArgs a) {
       int32_t st = PERM_OK;
       if (sh.bad) st = PERM_EINVAL;
       else if (!sh.zero_row && sh.bound_log2 + n > 1000) st = PERM_ERANGE;
-      else if (*a.aborted) st = PERM_EABORTED;
+      else if (*a.aborted) st = stop_status(*a.aborted);
       const double f = (n & 1) ? 2.0 : -2.0;
-      a.out[0] = st != PERM_OK ? __longlong_as_double(0x7ff8000000000000ll)
-                 : (sh.zero_row ? 0.0 : (tot.hi + tot.lo) * f);
+      if (a.mode == 0) {
+        a.out[0] = st != PERM_OK ? __longlong_as_double(0x7ff8000000000000ll)
+                   : (sh.zero_row ? 0.0 : (tot.hi + tot.lo) * f);
+      } else {
+        a.out[0] = st != PERM_OK ? __longlong_as_double(0x7ff8000000000000ll) : (sh.zero_row ? 0.0 : tot.hi);
+        a.out[1] = (st != PERM_OK || sh.zero_row) ? 0.0 : tot.lo;
+      }
       if (a.status) *a.status = st;
       *a.counter = 0u;
     }
   }
 }
 
-__global__ void sparse_trivial_kernel(double* out, int32_t* status) {
+__global__ void sparse_trivial_kernel(int mode, double* out, int32_t* status) {
   if (threadIdx.x == 0) {
-    out[0] = 1.0;
+    if (mode == 0) out[0] = 1.0;
+    else out[0] = out[1] = 0.0;
     if (status) *status = PERM_OK;
   }
 }
 
-}  // namespace permgpu
-
-using namespace permgpu;
-
-extern "C" int perm_sparse(int n, const int32_t* cptrs, const int32_t* rids, const double* cvals, int64_t nnz,
-                           double* out, int32_t* status, void* stream) {
-  if (n < 0 || n > PERM_NMAX) return PERM_ERANGE;
-  if (!out || (n > 0 && !cptrs) || nnz < 0 || nnz > (int64_t)n * n || (nnz > 0 && (!rids || !cvals)))
-    return PERM_EINVAL;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (n == 0) {
-    sparse_trivial_kernel<<<1, 32, 0, s>>>(out, status);
-    return cudaGetLastError() == cudaSuccess ? PERM_OK : PERM_ECUDA;
-  }
+// One sparse launch over the steps [g0, g1) (mode 0: the permanent, 1: the
+// raw range sum).
+static int sparse_launch(int n, const int32_t* cptrs, const int32_t* rids, const double* cvals, int64_t nnz,
+                         uint64_t g0, uint64_t g1, int mode, int paper_order, double* out, int32_t* status,
+                         cudaStream_t s) {
   const size_t off_ent = ((sizeof(int32_t) * (n + 1) + 15) / 16) * 16;
   const size_t smem = off_ent + sizeof(SpEntry) * (size_t)nnz + sizeof(long long) * n +
                       sizeof(long long) * (size_t)n * kSpBlock;
@@ -372,10 +385,11 @@ extern "C" int perm_sparse(int n, const int32_t* cptrs, const int32_t* rids, con
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return PERM_ECUDA;
-  const uint64_t N = 1ull << (n - 1);
   const int grid_full = sms * nb;
-  const int c = plan_chunk_exponent(n, N, grid_full * kSpWarps);
-  const uint64_t nchunks = N >> c;
+  const int c = plan_chunk_exponent(n, g1 - g0, grid_full * kSpWarps);
+  const uint64_t k_begin = g0 >> c;
+  const uint64_t k_end = (g1 + (1ull << c) - 1) >> c;
+  const uint64_t nchunks = g1 > g0 ? k_end - k_begin : 0;
   const uint64_t need = ((nchunks + 31) / 32 + kSpWarps - 1) / kSpWarps;
   const int grid = (int)(need < (uint64_t)grid_full ? (need > 0 ? need : 1) : grid_full);
   void* ws = nullptr;
@@ -398,6 +412,11 @@ extern "C" int perm_sparse(int n, const int32_t* cptrs, const int32_t* rids, con
   args.nnz = (int)nnz;
   args.c = c;
   args.one = 1;
+  args.mode = mode;
+  args.paper_order = paper_order;
+  args.g_begin = g0;
+  args.g_end = g1;
+  args.k_begin = k_begin;
   args.nchunks = nchunks;
   args.part = static_cast<dd*>(ws);
   args.counter = counter;
@@ -405,6 +424,7 @@ extern "C" int perm_sparse(int n, const int32_t* cptrs, const int32_t* rids, con
   args.status = status;
   args.abort_word = current_abort_word();
   args.aborted = counter + 1;
+  args.budget_ns = current_time_budget();
   void* params[] = {&args};
   cudaError_t e = cudaLaunchKernel(reinterpret_cast<const void*>(ryser_sparse_kernel), dim3(grid), dim3(kSpBlock),
                                    params, smem, s);
@@ -414,4 +434,45 @@ extern "C" int perm_sparse(int n, const int32_t* cptrs, const int32_t* rids, con
     return PERM_ECUDA;
   }
   return PERM_OK;
+}
+
+static int sparse_check(int n, const int32_t* cptrs, const int32_t* rids, const double* cvals, int64_t nnz,
+                        const double* out) {
+  if (n < 0 || n > PERM_NMAX) return PERM_ERANGE;
+  if (!out || (n > 0 && !cptrs) || nnz < 0 || nnz > (int64_t)n * n || (nnz > 0 && (!rids || !cvals)))
+    return PERM_EINVAL;
+  return PERM_OK;
+}
+
+}  // namespace permgpu
+
+using namespace permgpu;
+
+extern "C" int perm_sparse(int n, const int32_t* cptrs, const int32_t* rids, const double* cvals, int64_t nnz,
+                           double* out, int32_t* status, void* stream) {
+  int rc = sparse_check(n, cptrs, rids, cvals, nnz, out);
+  if (rc) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (n == 0) {
+    sparse_trivial_kernel<<<1, 32, 0, s>>>(0, out, status);
+    return cudaGetLastError() == cudaSuccess ? PERM_OK : PERM_ECUDA;
+  }
+  return sparse_launch(n, cptrs, rids, cvals, nnz, 0, 1ull << (n - 1), 0, 0, out, status, s);
+}
+
+extern "C" int perm_sparse_range(int n, const int32_t* cptrs, const int32_t* rids, const double* cvals, int64_t nnz,
+                                 uint64_t g_begin, uint64_t g_end, int flags, double* partial, int32_t* status,
+                                 void* stream) {
+  int rc = sparse_check(n, cptrs, rids, cvals, nnz, partial);
+  if (rc) return rc;
+  if (flags & ~PERM_SPARSE_PAPER_ORDER) return PERM_EINVAL;
+  const uint64_t N = n > 0 ? 1ull << (n - 1) : 0;
+  if (g_begin > g_end || g_end > N) return PERM_ERANGE;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (n == 0 || g_begin == g_end) {
+    sparse_trivial_kernel<<<1, 32, 0, s>>>(1, partial, status);
+    return cudaGetLastError() == cudaSuccess ? PERM_OK : PERM_ECUDA;
+  }
+  return sparse_launch(n, cptrs, rids, cvals, nnz, g_begin, g_end, 1, (flags & PERM_SPARSE_PAPER_ORDER) ? 1 : 0,
+                       partial, status, s);
 }

@@ -23,10 +23,15 @@ Tasks (all sums are over Alg. 1's Gray steps g in [g0, g1); see oracle/):
   boson_kKK_iII     the batched boson workload (8192 matrices, k in 8..26):
                     for every k, the first two matrices of that order,
                     complex double-double sweeps with S, W.
-  sparse44_range    sparse n = 44 (density 0.2): Alg. 2 on CRS/CCS over the
-                    2^30 steps [2^42, 2^42 + 2^30) (ryser_f64 arithmetic;
-                    spa_ryser_range), the full 2^43 steps being out of reach
-                    of the CPU.
+  bosonT_kKK_iII    the same matrices transposed (their permanent is the same;
+                    S and W of the transposed sweep bound the sweeps over the
+                    columns that the row-labelled batched plans run).
+  sparse44_range    sparse n = 44 (density 0.2): the 2^30 steps
+                    [2^42, 2^42 + 2^30) of the sweep in Alg. 2's column order
+                    (the same Gray steps as Alg. 1 on the dense form; zero
+                    entries add nothing), double-double with S, W on the dense
+                    form (ryser_dd_stats_range).  The full 2^43 steps are out
+                    of reach of the CPU.
 
 Every part runs with a fixed thread count (16), so its value does not depend
 on the machine's core count.  Finished tasks are skipped; --only selects
@@ -92,7 +97,10 @@ def tasks():
     out["cplx32"] = lambda: _cdd(syn.complex_32(), 0, 1 << 31)
     for i, k in boson_selection()[1]:
         out[f"boson_k{k:02d}_i{i:04d}"] = (lambda i=i: _cdd(syn.batched_boson()[i], 0, 1 << (syn.batched_boson()[i].shape[0] - 1), index=i))
-    out["sparse44_range"] = lambda: _sparse(syn.sparse_44(), 1 << 42, (1 << 42) + (1 << 30))
+    for i, k in boson_selection()[1]:
+        out[f"bosonT_k{k:02d}_i{i:04d}"] = (lambda i=i: _cdd(np.ascontiguousarray(syn.batched_boson()[i].T), 0,
+                                                              1 << (syn.batched_boson()[i].shape[0] - 1), index=i))
+    out["sparse44_range"] = lambda: _dd_stats(syn.sparse_44(), 1 << 42, (1 << 42) + (1 << 30))
     return out
 
 
@@ -122,13 +130,6 @@ def _bin_range(A, g0, g1):
     v = oracle.ryser_bin_range(A, g0, g1, threads=THREADS)
     return {"call": f"oracle.ryser_bin_range(A, {g0}, {g1}, threads={THREADS})", "n": A.shape[0], "g0": g0,
             "g1": g1, "sha256": digest(A), "sum_mod_2^128": str(v)}
-
-
-def _sparse(A, g0, g1):
-    crs, ccs = oracle.to_crs_ccs(A)
-    hi, lo = oracle.spa_ryser_range(A.shape[0], crs, ccs, g0, g1, threads=THREADS)
-    return {"call": f"oracle.spa_ryser_range(n, crs, ccs, {g0}, {g1}, threads={THREADS})", "n": A.shape[0],
-            "g0": g0, "g1": g1, "sha256": digest(A), "hi": fx(hi), "lo": fx(lo)}
 
 
 def load(path=GOLDEN) -> dict:

@@ -232,3 +232,55 @@ def test_auto_labels_match_the_drawn_modes(pg):
     assert np.array_equal(by_mode, auto)
     with pytest.raises(ValueError):
         pg.BatchPlan(mats[:2], row_labels="modes")
+
+
+def test_per_call_buffers(pg, oracle):
+    """perm_batched with buffers of the call: a second input laid out like the
+    first is read instead of the plan's own, results go to the given output,
+    and a call without buffers goes back to the plan's (no new plan, no
+    capture)."""
+    import torch
+
+    m1 = syn.boson_submatrices(120, 61, 6, 18, 64)
+    m2 = [0.3 * syn.complex_uniform(a.shape[0], 6200 + i) for i, a in enumerate(m1)]
+    plan = pg.BatchPlan(m1)
+    first = plan.run()
+    A2 = torch.from_numpy(np.concatenate([b.reshape(-1) for b in m2]).astype(np.complex128)).cuda()
+    out2 = torch.zeros_like(plan.out)
+    st2 = torch.full_like(plan.status, -1)
+    plan.run_async(A=A2, out=out2, status=st2)
+    torch.cuda.synchronize()
+    assert (st2 == 0).all()
+    o = out2.cpu().numpy()
+    got2 = o[0::2] + 1j * o[1::2]
+    for m, g in zip(m2, got2):
+        assert abs(g - oracle.perm_dp_c128(m)) <= 1e-12 * max(1.0, oracle.perm_dp_f64(np.abs(m)))
+    assert np.array_equal(plan.run(), first)  # the plan's own buffers again
+    plan.close()
+
+
+def test_large_k_chunked_vs_oracle_every_order(pg, oracle):
+    """Chunked lane-pair sweeps of orders 19..26 (the orders that carry most of
+    the boson batch's work), plain and row-labelled, against the oracle's
+    complex double-double sweep, within the bound of tests/_bounds.py (for the
+    labelled plan, the larger of the bounds of A and of its transpose)."""
+    from _bounds import complex_sweep_bound, dd_oracle_bound
+
+    mats, rows = syn.boson_submatrices(16, 63, 19, 26, 256, with_rows=True)
+    assert sorted({m.shape[0] for m in mats})[0] <= 20 and max(m.shape[0] for m in mats) >= 25
+    plain = pg.BatchPlan(mats)
+    lab = pg.BatchPlan(mats, row_labels=rows)
+    rp, rl = plain.run(), lab.run()
+    plain.close()
+    lab.close()
+    for m, a, b in zip(mats, rp, rl):
+        k = m.shape[0]
+        f = 2 * (-1) ** (k - 1)
+        o = oracle.ryser_cdd_range(m, 0, 1 << (k - 1))
+        t = oracle.ryser_cdd_range(np.ascontiguousarray(m.T), 0, 1 << (k - 1))
+        want = complex(o["re_hi"] + o["re_lo"], o["im_hi"] + o["im_lo"]) * f
+        tol_a = 2 * (complex_sweep_bound(o["S"], o["W"], k) + dd_oracle_bound(o["S"], k))
+        tol_t = 2 * (complex_sweep_bound(t["S"], t["W"], k) + dd_oracle_bound(t["S"], k))
+        ulp = 2.0 ** -52 * abs(want)
+        assert abs(a - want) <= np.sqrt(2) * tol_a + ulp, (k, a, want, tol_a)
+        assert abs(b - want) <= np.sqrt(2) * max(tol_a, tol_t) + ulp, (k, b, want, tol_t)

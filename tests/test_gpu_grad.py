@@ -285,3 +285,41 @@ def test_mixed_orders(pg, oracle):
         assert abs(p - oracle.perm_c128(M)) <= 1e-12
         _, Gs = pg.perm_grad(_dev(M))
         assert np.max(np.abs(G - Gs.cpu().numpy())) <= 1e-13
+
+
+def test_gradient_plan_runs_without_allocating(pg, oracle):
+    """perm_grad_plan_*: the buffers are allocated at creation; runs on other
+    inputs of the same shapes reuse them and give the results of
+    perm_grad_batched_mixed bit for bit (the same kernels and launch shapes)."""
+    import torch
+
+    g = syn.rng(12700)
+    ks = [5, 11, 0, 16, 11, 2, 20]
+    offs, tot = [], 0
+    for k in ks:
+        offs.append(tot)
+        tot += k * k
+    plan = pg.GradPlan(ks)
+    for rep in range(3):
+        mats = [2.0 * g.random((k, k)) - 1.0 for k in ks]
+        A = torch.zeros(max(tot, 1), dtype=torch.float64, device="cuda")
+        for M, o in zip(mats, offs):
+            A[o:o + M.size] = torch.from_numpy(M.reshape(-1))
+        Gp = torch.zeros_like(A)
+        out = torch.zeros(len(ks), dtype=torch.float64, device="cuda")
+        st = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+        before = torch.cuda.memory_allocated()
+        plan.run_async(A, out, Gp, st)
+        torch.cuda.synchronize()
+        assert torch.cuda.memory_allocated() == before
+        assert int(st.item()) == 0
+        perms, grads = pg.perm_grad_mixed(mats)
+        assert np.array_equal(out.cpu().numpy(), perms)
+        Gh = Gp.cpu().numpy()
+        for M, o, G in zip(mats, offs, grads):
+            k = M.shape[0]
+            assert np.array_equal(Gh[o:o + k * k].reshape(k, k), G)
+            if k:
+                assert abs(out.cpu().numpy()[ks.index(k)] - oracle.perm_dp_f64(mats[ks.index(k)])) <= \
+                    1e-12 * oracle.perm_dp_f64(np.abs(mats[ks.index(k)]))
+    plan.close()

@@ -134,3 +134,29 @@ def test_signed_and_dense_inputs_keep_their_accuracy(pg, oracle):
         assert abs(got - dense) <= 1e-12 * max(abs(want), 1e-300) + 1e-15 * scale
     J = np.ones((22, 22))
     assert pg.perm_sparse(*_ccs(J)) == pytest.approx(float(math.factorial(22)), rel=1e-13)
+
+
+@pytest.mark.parametrize("n,density", [(12, 0.3), (21, 0.2)])
+def test_range_partials(pg, oracle, n, density):
+    """perm_sparse_range: in Alg. 2's column order a range equals the oracle's
+    double-double sweep of the same steps; in the kernel's own order the
+    partials of any partition combine to perm_sparse's value; empty and bad
+    ranges are handled."""
+    from _bounds import dd_oracle_bound, real_rows_on_grid, real_sweep_bound
+
+    A = syn.sparse_real(n, 9300 + n, density)
+    nn, cp, ri, cv = _ccs(A)
+    N = 1 << (n - 1)
+    for g0, g1 in ((0, N), (0, 1), (3, 4), (N // 3, min(N, N // 3 + 4097)), (N - 100, N)):
+        hi, lo = pg.perm_sparse_range(nn, cp, ri, cv, g0, g1, paper_order=True)
+        o = oracle.ryser_dd_stats_range(A, g0, g1)
+        tol = real_sweep_bound(o["S"], o["W"], n, real_rows_on_grid(A)) + dd_oracle_bound(o["S"], n)
+        assert abs((hi + lo) - (o["hi"] + o["lo"])) <= tol + 1e-300, (g0, g1)
+    full = pg.perm_sparse(nn, cp, ri, cv)
+    cuts = [0, 5, N // 7, N // 2 + 3, N]
+    parts = [pg.perm_sparse_range(nn, cp, ri, cv, a, b) for a, b in zip(cuts[:-1], cuts[1:])]
+    assert pg.perm_combine(pg.PERM_F64, n, parts) == pytest.approx(full, rel=1e-13)
+    assert pg.perm_sparse_range(nn, cp, ri, cv, 7, 7) == (0.0, 0.0)
+    with pytest.raises(pg.PermError) as e:
+        pg.perm_sparse_range(nn, cp, ri, cv, 5, N + 1)
+    assert e.value.code == 2
