@@ -16,6 +16,8 @@ from __future__ import annotations
 
 import json
 
+import numpy as np
+
 from ._lib import PERM_BIN, PERM_C128, PERM_F64, PERM_F64X
 
 WORDS = {PERM_F64: 2, PERM_F64X: 2, PERM_C128: 4, PERM_BIN: 3}
@@ -142,23 +144,38 @@ def shard_matrices(ks, world: int, costs=None):
 
 
 def gather_results(dist, indices, values, count: int):
-    """All-gather every rank's (index, value) results (complex or real) and
-    return the `count` values in batch order on every rank."""
+    """All-gather every rank's (index, value) results and return the `count`
+    values in batch order on every rank: Python floats when every rank's
+    values are real (float64 results, PERM_F64X heads), complex numbers when
+    any rank has a complex one.  A rank may hold no matrices.  Indices travel
+    as int64, values as float64 pairs."""
     import torch
 
-    vals = [complex(v) for v in values]
-    local = torch.tensor([[float(i), v.real, v.imag] for i, v in zip(indices, vals)], dtype=torch.float64).reshape(-1, 3)
-    sizes = [torch.zeros(1, dtype=torch.int64) for _ in range(dist.get_world_size())]
-    dist.all_gather(sizes, torch.tensor([local.shape[0]], dtype=torch.int64))
-    width = max(int(s.item()) for s in sizes)
-    padded = torch.zeros((width, 3), dtype=torch.float64)
-    padded[: local.shape[0]] = local
-    outs = [torch.zeros_like(padded) for _ in sizes]
-    dist.all_gather(outs, padded)
+    vals = list(values)
+    idx = [int(i) for i in indices]
+    if len(vals) != len(idx):
+        raise ValueError("one value per index")
+    cplx_local = any(isinstance(v, complex) or np.iscomplexobj(v) for v in vals)
+    head = torch.tensor([len(idx), int(cplx_local)], dtype=torch.int64)
+    heads = [torch.zeros(2, dtype=torch.int64) for _ in range(dist.get_world_size())]
+    dist.all_gather(heads, head)
+    width = max(1, max(int(h[0]) for h in heads))  # never a zero-width exchange
+    cplx = any(int(h[1]) for h in heads)
+    pidx = torch.full((width,), -1, dtype=torch.int64)
+    pval = torch.zeros((width, 2), dtype=torch.float64)
+    for r, (i, v) in enumerate(zip(idx, vals)):
+        c = complex(v)
+        pidx[r] = i
+        pval[r, 0], pval[r, 1] = c.real, c.imag
+    oidx = [torch.zeros_like(pidx) for _ in heads]
+    oval = [torch.zeros_like(pval) for _ in heads]
+    dist.all_gather(oidx, pidx)
+    dist.all_gather(oval, pval)
     res = [None] * count
-    for o, sz in zip(outs, sizes):
-        for row in o[: int(sz.item())].tolist():
-            res[int(row[0])] = complex(row[1], row[2])
+    for h, ii, vv in zip(heads, oidx, oval):
+        for r in range(int(h[0])):
+            re, im = (float(x) for x in vv[r].tolist())
+            res[int(ii[r])] = complex(re, im) if cplx else re
     if any(v is None for v in res):
         raise ValueError("some matrices were computed by no rank")
     return res

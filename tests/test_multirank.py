@@ -203,3 +203,90 @@ def test_two_ranks_share_a_batch(oracle):
         got = list(results)
     mats = syn.boson_submatrices(30, 31, 3, 10, 32)
     assert got == [oracle.perm_dp_c128(x) for x in mats]
+
+
+def _real_batch_worker(rank, world, port, results):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import oracle
+        from paper_2502_16577_gb300 import ranges
+
+        mats = [syn.signed_real(k, 40 + k) for k in (5, 9)]  # two matrices, three ranks
+        mine = ranges.shard_matrices([m.shape[0] for m in mats], world)[rank]
+        vals = [oracle.perm_dp_f64(mats[i]) for i in mine]  # stands in for this rank's real batched plan
+        res = ranges.gather_results(dist, mine, vals, len(mats))
+        results.append((rank, len(mine), res))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_real_results_and_an_empty_shard(oracle):
+    """More ranks than matrices: one rank holds no matrix; real values come
+    back as floats in batch order on every rank."""
+    ctx = mp.get_context("spawn")
+    port = _free_port_cache[0]
+    with ctx.Manager() as m:
+        results = m.list()
+        procs = [ctx.Process(target=_real_batch_worker, args=(r, 3, port, results)) for r in range(3)]
+        for p in procs:
+            p.start()
+        for p in procs:
+            p.join(120)
+            assert p.exitcode == 0
+        got = list(results)
+    mats = [syn.signed_real(k, 40 + k) for k in (5, 9)]
+    want = [oracle.perm_dp_f64(x) for x in mats]
+    assert sorted(n for _, n, _ in got) == [0, 1, 1]
+    for _, _, res in got:
+        assert res == want and all(isinstance(v, float) for v in res)
+
+
+def _gpu_batch_worker(rank, world, port, results):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import torch
+
+        import paper_2502_16577_gb300 as pg
+        from paper_2502_16577_gb300 import ranges
+
+        mats = syn.boson_submatrices(40, 33, 3, 16, 24)  # 24 modes: repeated rows are common
+        mine = ranges.shard_matrices([m.shape[0] for m in mats], world)[rank]
+        plan = pg.BatchPlan([mats[i] for i in mine], device=torch.device("cuda", 0), row_labels="auto")
+        vals = list(plan.run())
+        plan.close()
+        res = ranges.gather_results(dist, mine, vals, len(mats))
+        if rank == 0:
+            results.extend(res)
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.gpu
+def test_two_ranks_batched_plans_on_one_gpu(oracle):
+    """Two gloo ranks on one GPU, each running the batched plan (rows labelled
+    by equality) on its share of the batch; the gathered results match the
+    oracle.  The ranks' launches are independent: nothing waits on the other."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2502_16577_gb300 import build
+
+    build.build()
+    ctx = mp.get_context("spawn")
+    port = _free_port_cache[0]
+    with ctx.Manager() as m:
+        results = m.list()
+        procs = [ctx.Process(target=_gpu_batch_worker, args=(r, 2, port, results)) for r in range(2)]
+        for p in procs:
+            p.start()
+        for p in procs:
+            p.join(300)
+            assert p.exitcode == 0
+        got = list(results)
+    mats = syn.boson_submatrices(40, 33, 3, 16, 24)
+    for x, g in zip(mats, got):
+        assert abs(g - oracle.perm_dp_c128(x)) <= 1e-10 * oracle.perm_dp_f64(np.abs(x))
