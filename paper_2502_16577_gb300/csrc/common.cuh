@@ -130,6 +130,51 @@ __device__ __forceinline__ int32_t stop_status(unsigned int flag) {
   return (flag & 1u) ? PERM_EABORTED : (flag & 2u) ? PERM_ETIMEOUT : PERM_OK;
 }
 
+// ------------------------------------------------ exact column equilibration
+
+// Columns whose largest |entry| (complex: the larger part) lies more than
+// 2^kColGap below the largest column's are scaled by the power of two 2^c_j
+// that brings them level with it; perm(A diag(2^c)) = perm(A) 2^(sum c), so the
+// sum is taken back out of the result's exponent (exact).  The rows are then
+// rounded to a fixed point relative to their absolute sums: without the scale,
+// the entries of a column far below the others would keep few bits there (or
+// none), with it every column keeps at least 61 - 8 - log2(n) bits.  Columns
+// within 2^kColGap of the largest keep c_j = 0, so such matrices are staged
+// exactly as without equilibration.
+constexpr int kColGap = 8;
+
+// W = 1: real entries A[i n + j]; W = 2: (re, im) pairs.  Threads j < n each
+// scan one column; c[j] receives the exponent shift.  Returns sum_j c_j (the
+// same in every thread).  Contains __syncthreads().
+template <int W>
+__device__ __forceinline__ int column_scales(const double* __restrict__ A, int n, int* c) {
+  __shared__ int s_emax, s_csum;
+  if (threadIdx.x == 0) {
+    s_emax = -100000;
+    s_csum = 0;
+  }
+  __syncthreads();
+  int e = -100000;  // a zero (or non-finite) column: no scale
+  const int j = threadIdx.x;
+  if (j < n) {
+    double m = 0.0;
+    for (int i = 0; i < n; ++i)
+      for (int w = 0; w < W; ++w) m = fmax(m, fabs(A[((size_t)i * n + j) * W + w]));
+    if (m > 0.0 && isfinite(m)) {
+      frexp(m, &e);
+      atomicMax(&s_emax, e);
+    }
+  }
+  __syncthreads();
+  if (j < n) {
+    const int cj = (e > -100000 && s_emax - e > kColGap) ? s_emax - e : 0;
+    c[j] = cj;
+    if (cj) atomicAdd(&s_csum, cj);
+  }
+  __syncthreads();
+  return s_csum;
+}
+
 // Gray code of step g (Sec. 2): bit j set <=> column j is in the subset.
 __device__ __forceinline__ uint64_t gray64(uint64_t g) { return g ^ (g >> 1); }
 

@@ -103,10 +103,11 @@ struct CplxLayout {
 };
 
 struct CplxShared {
-  int sum_s;
-  int bound_log2;
+  int sum_s;       // row scales plus column scales
+  int bound_log2;  // sum of k_i - 1 minus the column scales
   int nonfinite;
   int zero_row;
+  int cexp[64];    // column scales (exact column equilibration)
 };
 
 // Q_ij = round(a_ij 2^s_i) (both parts), s_i = 60 - k_i with
@@ -117,9 +118,10 @@ __device__ __forceinline__ void cplx_stage(const double* __restrict__ A, unsigne
   longlong2* D = reinterpret_cast<longlong2*>(smem + Lo::kD);
   longlong2* base = reinterpret_cast<longlong2*>(smem + Lo::kBase);
   longlong2* zero = reinterpret_cast<longlong2*>(smem + Lo::kZero);
+  const int csum = column_scales<2>(A, N, sh.cexp);
   if (threadIdx.x == 0) {
-    sh.sum_s = 0;
-    sh.bound_log2 = 0;
+    sh.sum_s = csum;
+    sh.bound_log2 = -csum;
     sh.nonfinite = 0;
     sh.zero_row = 0;
   }
@@ -132,22 +134,22 @@ __device__ __forceinline__ void cplx_stage(const double* __restrict__ A, unsigne
     for (int j = 0; j < 2 * N; ++j) {
       double v = row[j];
       fin &= isfinite(v) ? 1 : 0;
-      absum += fabs(v);
+      absum += ldexp(fabs(v), sh.cexp[j >> 1]);
     }
     int k = 0;
     if (fin && absum > 0.0) frexp(absum, &k);
     const int s = 60 - k;
     long long sr = 0, si = 0;
     for (int j = 0; j < N - 1; ++j) {
-      long long qr = fin ? __double2ll_rn(ldexp(row[2 * j], s)) : 0;
-      long long qi = fin ? __double2ll_rn(ldexp(row[2 * j + 1], s)) : 0;
+      long long qr = fin ? __double2ll_rn(ldexp(row[2 * j], s + sh.cexp[j])) : 0;
+      long long qi = fin ? __double2ll_rn(ldexp(row[2 * j + 1], s + sh.cexp[j])) : 0;
       sr += qr;
       si += qi;
       D[(2 * j) * N + i] = make_longlong2(2 * qr, 2 * qi);
       D[(2 * j + 1) * N + i] = make_longlong2(-2 * qr, -2 * qi);
     }
-    long long nr = fin ? __double2ll_rn(ldexp(row[2 * (N - 1)], s)) : 0;
-    long long ni = fin ? __double2ll_rn(ldexp(row[2 * (N - 1) + 1], s)) : 0;
+    long long nr = fin ? __double2ll_rn(ldexp(row[2 * (N - 1)], s + sh.cexp[N - 1])) : 0;
+    long long ni = fin ? __double2ll_rn(ldexp(row[2 * (N - 1) + 1], s + sh.cexp[N - 1])) : 0;
     base[i] = make_longlong2(nr - sr, ni - si);
     zero[i] = make_longlong2(0, 0);
     atomicAdd(&sh.sum_s, s);

@@ -120,10 +120,11 @@ struct RealLayout {
 };
 
 struct RealShared {
-  int sum_s;       // sum of the row scale exponents s_i
-  int bound_log2;  // sum of k_i - 1, k_i = binary exponent of row i's absolute sum
+  int sum_s;       // sum of the row scale exponents s_i, plus the column scales
+  int bound_log2;  // sum of k_i - 1 (row i's absolute sum in [2^(k_i-1), 2^k_i)) minus the column scales
   int nonfinite;
   int zero_row;
+  int cexp[64];    // column scales (exact column equilibration)
 };
 
 // Stage A into shared memory as fixed-point column increments.
@@ -139,9 +140,10 @@ __device__ __forceinline__ void real_stage(const double* __restrict__ A, unsigne
   long long* D = reinterpret_cast<long long*>(smem + L::kD);
   long long* base = reinterpret_cast<long long*>(smem + L::kBase);
   long long* zero = reinterpret_cast<long long*>(smem + L::kZero);
+  const int csum = column_scales<1>(A, N, sh.cexp);
   if (threadIdx.x == 0) {
-    sh.sum_s = 0;
-    sh.bound_log2 = 0;
+    sh.sum_s = csum;
+    sh.bound_log2 = -csum;
     sh.nonfinite = 0;
     sh.zero_row = 0;
   }
@@ -154,20 +156,20 @@ __device__ __forceinline__ void real_stage(const double* __restrict__ A, unsigne
     for (int j = 0; j < N; ++j) {
       double a = row[j];
       fin &= isfinite(a) ? 1 : 0;
-      absum += fabs(a);
+      absum += ldexp(fabs(a), sh.cexp[j]);
     }
     int k = 0;
     if (fin && absum > 0.0) frexp(absum, &k);
     int s = 61 - k;
     long long qsum = 0;
     for (int j = 0; j < N - 1; ++j) {
-      long long q = fin ? __double2ll_rn(ldexp(row[j], s - 1)) : 0;
+      long long q = fin ? __double2ll_rn(ldexp(row[j], s - 1 + sh.cexp[j])) : 0;
       long long Q = 2 * q;
       qsum += Q;
       D[(2 * j) * L::NP + i] = 2 * Q;
       D[(2 * j + 1) * L::NP + i] = -2 * Q;
     }
-    long long qn = fin ? 2 * __double2ll_rd(ldexp(row[N - 1], s - 1)) + 1 : 1;
+    long long qn = fin ? 2 * __double2ll_rd(ldexp(row[N - 1], s - 1 + sh.cexp[N - 1])) + 1 : 1;
     base[i] = qn - qsum;
     zero[i] = 0;
     atomicAdd(&sh.sum_s, s);

@@ -157,10 +157,10 @@ __device__ __forceinline__ void realx_exact_last_column(const double* __restrict
   if (i < N && !sh.nonfinite) {
     const double* row = A + (size_t)i * N;
     double absum = 0.0;
-    for (int j = 0; j < N; ++j) absum += fabs(row[j]);
+    for (int j = 0; j < N; ++j) absum += ldexp(fabs(row[j]), sh.cexp[j]);  // as real_stage
     int k = 0;
     if (absum > 0.0) frexp(absum, &k);
-    const double v = ldexp(row[N - 1], 61 - k - 1);
+    const double v = ldexp(row[N - 1], 61 - k - 1 + sh.cexp[N - 1]);
     base[i] += 2 * __double2ll_rn(v) - (2 * __double2ll_rd(v) + 1);
   }
   __syncthreads();

@@ -116,13 +116,42 @@ __global__ void __launch_bounds__(kSpBlock) ryser_sparse_kernel(SpArgs a) {
       }
   }
   __syncthreads();
+  // exact column equilibration (see column_scales): thread j scans column j
+  __shared__ int s_cexp[64];
+  __shared__ int s_emax, s_csum;
+  if (threadIdx.x == 0) {
+    s_emax = -100000;
+    s_csum = 0;
+  }
+  __syncthreads();
+  int ecol = -100000;
+  if (!sh.bad && threadIdx.x < n) {
+    double m = 0.0;
+    for (int p = cp[threadIdx.x]; p < cp[threadIdx.x + 1]; ++p) m = fmax(m, fabs(a.cvals[p]));
+    if (m > 0.0 && isfinite(m)) {
+      frexp(m, &ecol);
+      atomicMax(&s_emax, ecol);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < n) {
+    const int cj = (ecol > -100000 && s_emax - ecol > kColGap) ? s_emax - ecol : 0;
+    s_cexp[threadIdx.x] = cj;
+    if (cj) atomicAdd(&s_csum, cj);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    sh.sum_s = s_csum;
+    sh.bound_log2 = -s_csum;
+  }
+  __syncthreads();
   // row scales: thread i scans every column for row i (deterministic sums)
   if (!sh.bad && threadIdx.x < n) {
     const int i = threadIdx.x;
     double absum = 0.0;
     for (int j = 0; j < n; ++j)
       for (int p = cp[j]; p < cp[j + 1]; ++p)
-        if (a.rids[p] == i) absum += fabs(a.cvals[p]);
+        if (a.rids[p] == i) absum += ldexp(fabs(a.cvals[p]), s_cexp[j]);
     int k = 0;
     if (absum > 0.0) frexp(absum, &k);
     else atomicOr(&sh.zero_row, 1);
@@ -133,13 +162,14 @@ __global__ void __launch_bounds__(kSpBlock) ryser_sparse_kernel(SpArgs a) {
   __syncthreads();
   // column entries (2 Q_ij) and base_i = Q_{i,n-1} - sum_{j<n-1} Q_ij
   if (!sh.bad) {
-    for (int p = threadIdx.x; p < nnz; p += kSpBlock) {
-      int r = a.rids[p];
-      long long q = __double2ll_rn(ldexp(a.cvals[p], s_scale[r]));
-      ent[p].row = r;
-      ent[p].pad = 0;
-      ent[p].d = 2 * q;
-    }
+    for (int j = threadIdx.x; j < n; j += kSpBlock)
+      for (int p = cp[j]; p < cp[j + 1]; ++p) {
+        int r = a.rids[p];
+        long long q = __double2ll_rn(ldexp(a.cvals[p], s_scale[r] + s_cexp[j]));
+        ent[p].row = r;
+        ent[p].pad = 0;
+        ent[p].d = 2 * q;
+      }
   }
   __syncthreads();
   if (!sh.bad && threadIdx.x < n) {

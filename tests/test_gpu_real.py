@@ -188,3 +188,40 @@ def test_n40_config_sampled_range(pg, oracle):
     # binary64 sums of ~1.7e7 terms of rms ~3e10: allow 1e-9 relative to the
     # sum of |terms| bound used by the oracle's own rounding
     assert abs((hi + lo) - (ohi + olo)) <= 1e-9 * max(abs(ohi), 1.0) + 1e-6
+
+
+def test_columns_scaled_far_apart(pg, oracle):
+    """Columns scaled by powers of two far apart (2^-300, 2^+300, 2^-290, 2^+40):
+    perm(A diag(d)) = perm(A) prod d exactly, so the GPU result must match the
+    oracle on the unscaled matrix times the factor, to the same relative
+    accuracy as the unscaled matrix (exact column equilibration in staging).
+    Dense real, extended products, complex and sparse paths."""
+    import torch
+
+    n = 14
+    scales = np.ones(n)
+    scales[[2, 5, 9, 11]] = [2.0 ** -300, 2.0 ** 300, 2.0 ** -290, 2.0 ** 40]
+    factor_log2 = -300 + 300 - 290 + 40
+    P = syn.uniform_real(n, 7100)
+    want = math.ldexp(oracle.perm_dp_f64(P), factor_log2)
+    got = pg.perm(_dev(P * scales))
+    assert got == pytest.approx(want, rel=1e-13)
+    hi, lo = pg.perm_x(_dev(P * scales))
+    assert hi + lo == pytest.approx(want, rel=1e-13)
+    S = syn.signed_real(n, 7101)
+    ref = oracle.perm_dd(S)
+    got = pg.perm(_dev(S * scales))
+    assert abs(math.ldexp(got, -factor_log2) - (ref[0] + ref[1])) <= 1e-14 * oracle.perm_dp_f64(np.abs(S))
+    U = syn.haar_unitary(n, 7102)
+    gc = pg.perm(_dev(U * scales))
+    wc = oracle.perm_dp_c128(U)
+    assert abs(complex(math.ldexp(gc.real, -factor_log2), math.ldexp(gc.imag, -factor_log2)) - wc) <= 1e-13
+    Z = syn.sparse_real(n, 7103, 0.4)
+    cp, ri, cv = (torch.from_numpy(x).cuda() for x in syn.to_ccs(Z * scales))
+    gs = pg.perm_sparse(n, cp, ri, cv)
+    assert gs == pytest.approx(math.ldexp(oracle.perm_dp_f64(Z), factor_log2), rel=1e-13)
+    # a gap of at most 2^8 is left alone (the rows' own scales absorb it)
+    T = syn.uniform_real(n, 7104)
+    T2 = T.copy()
+    T2[:, 3] *= 2.0 ** 7
+    assert pg.perm(_dev(T2)) == pytest.approx(pg.perm(_dev(T)) * 2.0 ** 7, rel=1e-14)
