@@ -175,8 +175,8 @@ def run_reference(args):
 # capture of this kernel (smsp__inst_executed.sum x 32 / steps), with the
 # SHA-256 (first 16 hex digits) of the kernel source it was taken on.  The
 # issue view below is reported only while real.cuh still has that hash.
-REAL40_INST_PER_STEP = None
-REAL40_INST_SOURCE = None
+REAL40_INST_PER_STEP = 737.0
+REAL40_INST_SOURCE = "a448d8cbf4af8000"
 
 
 def kernel_source_hash() -> str:

@@ -84,7 +84,11 @@ typedef enum {
  *
  * Real and complex entries are converted once to 64-bit fixed point with a
  * power-of-two scale per row (error at most 2^-60 of the row's absolute sum)
- * and the row vector x is kept exactly; products carry 62-bit mantissas and
+ * and the row vector x is kept exactly; columns whose largest entry lies more
+ * than a factor 2 below the largest column's are first scaled by an exact
+ * power of two up to its level (perm(A D) = perm(A) det D for a diagonal D of
+ * powers of two, taken back out of the result exactly), which keeps their
+ * bits and avoids the cancellation a dominant column causes; products carry 62-bit mantissas and
  * the signed sum is accumulated in binary64 with a double-double carry.
  * PERM_F64X uses the same fixed-point rows (column n-1 rounded to nearest,
  * so a row is exact when every a_ij 2^(60-k) is an integer, k the binary

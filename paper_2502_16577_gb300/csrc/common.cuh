@@ -132,16 +132,21 @@ __device__ __forceinline__ int32_t stop_status(unsigned int flag) {
 
 // ------------------------------------------------ exact column equilibration
 
-// Columns whose largest |entry| (complex: the larger part) lies more than
-// 2^kColGap below the largest column's are scaled by the power of two 2^c_j
-// that brings them level with it; perm(A diag(2^c)) = perm(A) 2^(sum c), so the
-// sum is taken back out of the result's exponent (exact).  The rows are then
-// rounded to a fixed point relative to their absolute sums: without the scale,
-// the entries of a column far below the others would keep few bits there (or
-// none), with it every column keeps at least 61 - 8 - log2(n) bits.  Columns
-// within 2^kColGap of the largest keep c_j = 0, so such matrices are staged
-// exactly as without equilibration.
-constexpr int kColGap = 8;
+// Columns whose largest |entry| (complex: the larger part) lies more than a
+// factor 2^kColGap below the largest column's are scaled by the power of two
+// 2^c_j that brings them level with it; perm(A diag(2^c)) = perm(A) 2^(sum c),
+// so the sum is taken back out of the result's exponent (exact).  Two reasons:
+//  * the rows are rounded to a fixed point relative to their absolute sums, so
+//    without the scale the entries of a column far below the others keep few
+//    bits (or none);
+//  * a column far above the others dominates every row sum x_i, the terms of
+//    the sweep are then far larger than the permanent and cancel (with one
+//    column 2^7 above the rest, n = 14 loses 20 bits to cancellation);
+//    balanced columns avoid that.
+// Matrices whose column maxima lie within a factor 2 of each other (random
+// dense, Haar and the sparse workloads) keep c_j = 0: they are staged exactly
+// as without equilibration.
+constexpr int kColGap = 1;
 
 // W = 1: real entries A[i n + j]; W = 2: (re, im) pairs.  Threads j < n each
 // scan one column; c[j] receives the exponent shift.  Returns sum_j c_j (the
