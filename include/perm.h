@@ -113,7 +113,10 @@ int perm(const void* A, int n, int type, void* out, int32_t* status, void* strea
  *     PERM_BIN:  uint64_t[3] = sum_g (-1)^g prod_i x'_i(g) modulo 2^192,
  *                little-endian, with the doubled integer rows x' = 2x.
  *   x_i(g) is Alg. 1's row vector after the subsets up to Gray_g, with
- *   x_i(0) = a_{i,n-1} - (sum_j a_{i,j}) / 2.
+ *   x_i(0) = a_{i,n-1} - (sum_j a_{i,j}) / 2.  The matrix is staged without
+ *   perm()'s column equilibration, which changes individual terms: the
+ *   partials are sums of these very terms (only perm() of the whole sweep
+ *   balances the columns).
  *   status as for perm(); for PERM_BIN it reports PERM_EOVERFLOW when the
  *   combined sum may not determine perm(A) (the partial itself stays exact).
  */
@@ -162,7 +165,9 @@ int perm_sparse(int n, const int32_t* cptrs, const int32_t* rids, const double* 
  *       [0, 2^(n-1)) made with flags 0 combine to perm(A), as perm_sparse.
  *   flags PERM_SPARSE_PAPER_ORDER: Alg. 2's own order, Gray bit j <-> column j
  *       (the steps of perm_range on the dense form); slower at low density.
- * Partials combine with perm_combine(PERM_F64, ...).  status as perm_sparse;
+ * Like perm_range, ranges are staged without perm_sparse's column
+ * equilibration.  Partials combine with perm_combine(PERM_F64, ...).  status
+ * as perm_sparse;
  * PERM_EINVAL for unknown flags, PERM_ERANGE for a bad range.
  */
 #define PERM_SPARSE_PAPER_ORDER 1

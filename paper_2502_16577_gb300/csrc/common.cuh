@@ -148,11 +148,17 @@ __device__ __forceinline__ int32_t stop_status(unsigned int flag) {
 // as without equilibration.
 constexpr int kColGap = 1;
 
+// Only a sweep over all 2^(n-1) steps is equilibrated: the scale changes the
+// individual terms (only their full sum scales by 2^(sum c)), so range sums
+// (perm_range, perm_sparse_range, mode 1) stage the matrix unscaled and keep
+// the terms of Alg. 1.
+//
 // W = 1: real entries A[i n + j]; W = 2: (re, im) pairs.  Threads j < n each
-// scan one column; c[j] receives the exponent shift.  Returns sum_j c_j (the
-// same in every thread).  Contains __syncthreads().
+// scan one column; c[j] receives the exponent shift (0 everywhere unless
+// `apply`).  Returns sum_j c_j (the same in every thread).  Contains
+// __syncthreads().
 template <int W>
-__device__ __forceinline__ int column_scales(const double* __restrict__ A, int n, int* c) {
+__device__ __forceinline__ int column_scales(const double* __restrict__ A, int n, int* c, bool apply) {
   __shared__ int s_emax, s_csum;
   if (threadIdx.x == 0) {
     s_emax = -100000;
@@ -172,7 +178,7 @@ __device__ __forceinline__ int column_scales(const double* __restrict__ A, int n
   }
   __syncthreads();
   if (j < n) {
-    const int cj = (e > -100000 && s_emax - e > kColGap) ? s_emax - e : 0;
+    const int cj = (apply && e > -100000 && s_emax - e > kColGap) ? s_emax - e : 0;
     c[j] = cj;
     if (cj) atomicAdd(&s_csum, cj);
   }

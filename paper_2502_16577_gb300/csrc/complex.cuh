@@ -113,12 +113,13 @@ struct CplxShared {
 // Q_ij = round(a_ij 2^s_i) (both parts), s_i = 60 - k_i with
 // sum_j |re| + |im| in [2^(k_i-1), 2^k_i): |Y_i| <= 2^60 per part.
 template <int N>
-__device__ __forceinline__ void cplx_stage(const double* __restrict__ A, unsigned char* smem, CplxShared& sh) {
+__device__ __forceinline__ void cplx_stage(const double* __restrict__ A, unsigned char* smem, CplxShared& sh,
+                                           bool equilibrate) {
   using Lo = CplxLayout<N>;
   longlong2* D = reinterpret_cast<longlong2*>(smem + Lo::kD);
   longlong2* base = reinterpret_cast<longlong2*>(smem + Lo::kBase);
   longlong2* zero = reinterpret_cast<longlong2*>(smem + Lo::kZero);
-  const int csum = column_scales<2>(A, N, sh.cexp);
+  const int csum = column_scales<2>(A, N, sh.cexp, equilibrate);
   if (threadIdx.x == 0) {
     sh.sum_s = csum;
     sh.bound_log2 = -csum;
@@ -165,7 +166,7 @@ __global__ void __launch_bounds__(kBlock, (N <= 8 ? 2 : 1)) ryser_cplx_kernel(Ry
   using Lo = CplxLayout<N>;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ CplxShared sh;
-  cplx_stage<N>(static_cast<const double*>(a.A), smem, sh);
+  cplx_stage<N>(static_cast<const double*>(a.A), smem, sh, a.mode == 0);
   const longlong2* D = reinterpret_cast<const longlong2*>(smem + Lo::kD);
   const longlong2* base = reinterpret_cast<const longlong2*>(smem + Lo::kBase);
   const longlong2* zero = reinterpret_cast<const longlong2*>(smem + Lo::kZero);
@@ -344,7 +345,7 @@ __global__ void __launch_bounds__(kBlock, 2) ryser_cplx2_kernel(RyserArgs a) {
   using Lo = CplxLayout<N>;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ CplxShared sh;
-  cplx_stage<N>(static_cast<const double*>(a.A), smem, sh);
+  cplx_stage<N>(static_cast<const double*>(a.A), smem, sh, a.mode == 0);
   const longlong2* D = reinterpret_cast<const longlong2*>(smem + Lo::kD);
   const longlong2* base = reinterpret_cast<const longlong2*>(smem + Lo::kBase);
   const bool bad = sh.nonfinite || sh.bound_log2 + N > 1000;

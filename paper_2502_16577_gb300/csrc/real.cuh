@@ -135,12 +135,13 @@ struct RealShared {
 //   or j = n-1, else -1)  represents x'_i = 2 x_i scaled by 2^s_i, and
 //   |Y_i| <= sum_j |Q_ij| < 2^61 + n.
 template <int N>
-__device__ __forceinline__ void real_stage(const double* __restrict__ A, unsigned char* smem, RealShared& sh) {
+__device__ __forceinline__ void real_stage(const double* __restrict__ A, unsigned char* smem, RealShared& sh,
+                                           bool equilibrate) {
   using L = RealLayout<N>;
   long long* D = reinterpret_cast<long long*>(smem + L::kD);
   long long* base = reinterpret_cast<long long*>(smem + L::kBase);
   long long* zero = reinterpret_cast<long long*>(smem + L::kZero);
-  const int csum = column_scales<1>(A, N, sh.cexp);
+  const int csum = column_scales<1>(A, N, sh.cexp, equilibrate);
   if (threadIdx.x == 0) {
     sh.sum_s = csum;
     sh.bound_log2 = -csum;
@@ -200,7 +201,7 @@ __global__ void __launch_bounds__(kBlock, (kRealStepPairs<N> ? 1 : 2)) ryser_rea
   using L = RealLayout<N>;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ RealShared sh;
-  real_stage<N>(static_cast<const double*>(a.A), smem, sh);
+  real_stage<N>(static_cast<const double*>(a.A), smem, sh, a.mode == 0);
   const long long* D = reinterpret_cast<const long long*>(smem + L::kD);
   const long long* base = reinterpret_cast<const long long*>(smem + L::kBase);
   const long long* zero = reinterpret_cast<const long long*>(smem + L::kZero);

@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(kBlock, (N <= 40 ? 2 : 1)) ryser_realx_kernel(
   using L = RealLayout<N>;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ RealShared sh;
-  real_stage<N>(static_cast<const double*>(a.A), smem, sh);
+  real_stage<N>(static_cast<const double*>(a.A), smem, sh, a.mode == 0);
   realx_exact_last_column<N>(static_cast<const double*>(a.A), smem, sh);
   const long long* D = reinterpret_cast<const long long*>(smem + L::kD);
   const long long* base = reinterpret_cast<const long long*>(smem + L::kBase);

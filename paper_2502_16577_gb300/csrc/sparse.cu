@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(kSpBlock) ryser_sparse_kernel(SpArgs a) {
       }
   }
   __syncthreads();
-  // exact column equilibration (see column_scales): thread j scans column j
+  // exact column equilibration, full sweeps only (see column_scales): thread j scans column j
   __shared__ int s_cexp[64];
   __shared__ int s_emax, s_csum;
   if (threadIdx.x == 0) {
@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(kSpBlock) ryser_sparse_kernel(SpArgs a) {
   }
   __syncthreads();
   if (threadIdx.x < n) {
-    const int cj = (ecol > -100000 && s_emax - ecol > kColGap) ? s_emax - ecol : 0;
+    const int cj = (a.mode == 0 && ecol > -100000 && s_emax - ecol > kColGap) ? s_emax - ecol : 0;
     s_cexp[threadIdx.x] = cj;
     if (cj) atomicAdd(&s_csum, cj);
   }
