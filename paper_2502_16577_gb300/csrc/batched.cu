@@ -127,9 +127,10 @@ __device__ __forceinline__ int batch_labels_differ(const BatchArgs& a, const Bat
 
 // Transposed unit: factor i is column i of A; the toggles are rows, the
 // base holds the fixed row and the repeated rows times their coefficients.
-// Scales, rounding and the odd fixed row (real) follow the plain branch.
+// Scales, rounding and the odd fixed row (real) follow the plain branch; row r
+// of A is scaled by 2^cexp[r] (equal rows get equal scales).
 __device__ void batch_prep_transposed(const BatchArgs& a, const BatchMat& bm, int& s_sum, int& s_bound,
-                                      int& s_flags) {
+                                      int& s_flags, const int* cexp) {
   const int k = bm.k;
   const int32_t* d = a.desc + bm.desc;
   const int f = d[0], G = d[1];
@@ -147,7 +148,7 @@ __device__ void batch_prep_transposed(const BatchArgs& a, const BatchMat& bm, in
     for (int q = 0; q < w; ++q) {
       const double v = col[(int64_t)w * r * k + q];
       fin &= isfinite(v) ? 1 : 0;
-      absum += fabs(v);
+      absum += ldexp(fabs(v), cexp[r]);
     }
   const int bad = batch_labels_differ(a, bm, i);
   int kk = 0;
@@ -157,8 +158,8 @@ __device__ void batch_prep_transposed(const BatchArgs& a, const BatchMat& bm, in
     long long* RD = reinterpret_cast<long long*>(a.table + bm.d_off);
     long long* rbase = reinterpret_cast<long long*>(a.table + bm.b_off);
     const int s = 61 - kk;
-    auto q_of = [&](int r) { return fin ? __double2ll_rn(ldexp(col[(int64_t)r * k], s - 1)) : 0ll; };
-    long long b = fin ? 2 * __double2ll_rd(ldexp(col[(int64_t)f * k], s - 1)) + 1 : 1;
+    auto q_of = [&](int r) { return fin ? __double2ll_rn(ldexp(col[(int64_t)r * k], s - 1 + cexp[r])) : 0ll; };
+    long long b = fin ? 2 * __double2ll_rd(ldexp(col[(int64_t)f * k], s - 1 + cexp[f])) + 1 : 1;
     for (int j = 0; j < k - 1; ++j) {
       const long long q = j < G ? q_of(tg[j]) : 0;
       b -= 2 * q;
@@ -176,7 +177,7 @@ __device__ void batch_prep_transposed(const BatchArgs& a, const BatchMat& bm, in
     longlong2* base = a.table + bm.b_off;
     const int s = 60 - kk;
     auto q_of = [&](int r, int part) {
-      return fin ? __double2ll_rn(ldexp(col[(int64_t)2 * r * k + part], s)) : 0ll;
+      return fin ? __double2ll_rn(ldexp(col[(int64_t)2 * r * k + part], s + cexp[r])) : 0ll;
     };
     long long br = q_of(f, 0), bi = q_of(f, 1);
     for (int j = 0; j < k - 1; ++j) {
@@ -210,7 +211,7 @@ __global__ void __launch_bounds__(kBlock) batch_prep_kernel(BatchArgs a) {
   longlong2* D = a.table + bm.d_off;
   longlong2* base = a.table + bm.b_off;
   longlong2* zero = base + k;
-  __shared__ int s_sum, s_bound, s_flags;
+  __shared__ int s_sum, s_bound, s_flags, s_cexp[64];
   if (threadIdx.x == 0) {
     s_sum = 0;
     s_bound = 0;
@@ -218,8 +219,13 @@ __global__ void __launch_bounds__(kBlock) batch_prep_kernel(BatchArgs a) {
   }
   __syncthreads();
   const int i = threadIdx.x;
-  if (bm.desc >= 0) {
-    batch_prep_transposed(a, bm, s_sum, s_bound, s_flags);
+  // exact equilibration of the toggled lines (columns; rows of a transposed
+  // unit): the sweep sums 2^(sum c) perm, undone through sum_s
+  const bool tr = bm.desc >= 0;
+  const int csum = a.type == PERM_F64 ? column_scales<1>(a.A + bm.a_off, k, s_cexp, true, tr)
+                                      : column_scales<2>(a.A + 2 * bm.a_off, k, s_cexp, true, tr);
+  if (tr) {
+    batch_prep_transposed(a, bm, s_sum, s_bound, s_flags, s_cexp);
   } else if (a.type == PERM_F64) {
     // real: odd fixed-point rows as in real_stage (Y = 2 x 2^s)
     long long* RD = reinterpret_cast<long long*>(a.table + bm.d_off);
@@ -232,19 +238,19 @@ __global__ void __launch_bounds__(kBlock) batch_prep_kernel(BatchArgs a) {
       for (int j = 0; j < k; ++j) {
         const double v = row[j];
         fin &= isfinite(v) ? 1 : 0;
-        absum += fabs(v);
+        absum += ldexp(fabs(v), s_cexp[j]);
       }
       int kk = 0;
       if (fin && absum > 0.0) frexp(absum, &kk);
       const int s = 61 - kk;
       long long qsum = 0;
       for (int j = 0; j < k - 1; ++j) {
-        const long long q = fin ? __double2ll_rn(ldexp(row[j], s - 1)) : 0;
+        const long long q = fin ? __double2ll_rn(ldexp(row[j], s - 1 + s_cexp[j])) : 0;
         qsum += 2 * q;
         RD[(2 * j) * k + i] = 4 * q;
         RD[(2 * j + 1) * k + i] = -4 * q;
       }
-      const long long qn = fin ? 2 * __double2ll_rd(ldexp(row[k - 1], s - 1)) + 1 : 1;
+      const long long qn = fin ? 2 * __double2ll_rd(ldexp(row[k - 1], s - 1 + s_cexp[k - 1])) + 1 : 1;
       rbase[i] = qn - qsum;
       rzero[i] = 0;
       atomicAdd(&s_sum, s);
@@ -259,22 +265,22 @@ __global__ void __launch_bounds__(kBlock) batch_prep_kernel(BatchArgs a) {
     for (int j = 0; j < 2 * k; ++j) {
       double v = row[j];
       fin &= isfinite(v) ? 1 : 0;
-      absum += fabs(v);
+      absum += ldexp(fabs(v), s_cexp[j / 2]);
     }
     int kk = 0;
     if (fin && absum > 0.0) frexp(absum, &kk);
     const int s = 60 - kk;
     long long sr = 0, si = 0;
     for (int j = 0; j < k - 1; ++j) {
-      long long qr = fin ? __double2ll_rn(ldexp(row[2 * j], s)) : 0;
-      long long qi = fin ? __double2ll_rn(ldexp(row[2 * j + 1], s)) : 0;
+      long long qr = fin ? __double2ll_rn(ldexp(row[2 * j], s + s_cexp[j])) : 0;
+      long long qi = fin ? __double2ll_rn(ldexp(row[2 * j + 1], s + s_cexp[j])) : 0;
       sr += qr;
       si += qi;
       D[(2 * j) * k + i] = make_longlong2(2 * qr, 2 * qi);
       D[(2 * j + 1) * k + i] = make_longlong2(-2 * qr, -2 * qi);
     }
-    long long nr = fin ? __double2ll_rn(ldexp(row[2 * (k - 1)], s)) : 0;
-    long long ni = fin ? __double2ll_rn(ldexp(row[2 * (k - 1) + 1], s)) : 0;
+    long long nr = fin ? __double2ll_rn(ldexp(row[2 * (k - 1)], s + s_cexp[k - 1])) : 0;
+    long long ni = fin ? __double2ll_rn(ldexp(row[2 * (k - 1) + 1], s + s_cexp[k - 1])) : 0;
     base[i] = make_longlong2(nr - sr, ni - si);
     zero[i] = make_longlong2(0, 0);
     atomicAdd(&s_sum, s);
@@ -285,8 +291,8 @@ __global__ void __launch_bounds__(kBlock) batch_prep_kernel(BatchArgs a) {
   __syncthreads();
   if (threadIdx.x == 0) {
     BatchMat* mm = const_cast<BatchMat*>(a.mats) + m;
-    mm->sum_s = s_sum;
-    mm->flags = s_flags | (s_bound + k > 1000 ? 4 : 0);
+    mm->sum_s = s_sum + csum;
+    mm->flags = s_flags | (s_bound - csum + k > 1000 ? 4 : 0);  // the range of A itself
   }
 }
 

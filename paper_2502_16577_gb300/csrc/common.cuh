@@ -154,11 +154,13 @@ constexpr int kColGap = 1;
 // the terms of Alg. 1.
 //
 // W = 1: real entries A[i n + j]; W = 2: (re, im) pairs.  Threads j < n each
-// scan one column; c[j] receives the exponent shift (0 everywhere unless
-// `apply`).  Returns sum_j c_j (the same in every thread).  Contains
-// __syncthreads().
+// scan one column (`rows`: one row, for a sweep whose toggles are the rows of
+// A; perm(diag(2^c) A) = 2^(sum c) perm(A) as well); c[j] receives the
+// exponent shift (0 everywhere unless `apply`).  Returns sum_j c_j (the same
+// in every thread).  Contains __syncthreads().
 template <int W>
-__device__ __forceinline__ int column_scales(const double* __restrict__ A, int n, int* c, bool apply) {
+__device__ __forceinline__ int column_scales(const double* __restrict__ A, int n, int* c, bool apply,
+                                             bool rows = false) {
   __shared__ int s_emax, s_csum;
   if (threadIdx.x == 0) {
     s_emax = -100000;
@@ -170,7 +172,7 @@ __device__ __forceinline__ int column_scales(const double* __restrict__ A, int n
   if (j < n) {
     double m = 0.0;
     for (int i = 0; i < n; ++i)
-      for (int w = 0; w < W; ++w) m = fmax(m, fabs(A[((size_t)i * n + j) * W + w]));
+      for (int w = 0; w < W; ++w) m = fmax(m, fabs(A[((rows ? (size_t)j * n + i : (size_t)i * n + j)) * W + w]));
     if (m > 0.0 && isfinite(m)) {
       frexp(m, &e);
       atomicMax(&s_emax, e);

@@ -53,6 +53,7 @@ constexpr int kGWarps = 4;              // warps per CTA
 constexpr int kGThreads = 32 * kGWarps;
 constexpr int kGSub = kGWarps * 4;      // sub-groups per CTA
 constexpr int kDead = -1000000;         // exponent offset of rows that contribute nothing
+constexpr int kCsStride = 33;           // ints per matrix in GradArgs::cs (n <= 32, plus the sum)
 
 struct GradArgs {
   const double* A;    // count matrices, n*n scalars each (a scalar is 1 or 2 doubles)
@@ -67,6 +68,7 @@ struct GradArgs {
   const volatile uint32_t* abort_word;  // perm_set_abort_word (device view), or null
   uint64_t budget_ns;                   // perm_set_time_budget, 0: none
   uint32_t* stopped;                    // bit 0: aborted, bit 1: out of time (zeroed)
+  int* cs;            // [count][kCsStride]: column scales c_0..c_{n-1}, then their sum
 };
 
 // ------------------------------------------------------------ real values
@@ -245,14 +247,20 @@ __device__ __forceinline__ double2 asel(double2 a, bool keep) { return keep ? a 
 // One matrix into shared memory as signed column increments (both element
 // types: Y_i = 2 x_i 2^(s_i), x_i in units of 2^(-s_i - 1)).  Real rows round
 // column n-1 to odd multiples (|Y_i| is then never zero, as in the forward
-// kernel); padded rows are the constant 1.
+// kernel); padded rows are the constant 1.  Columns far below the largest are
+// first scaled by exact powers of two, A' = A diag(2^c) (s_cexp, their sum in
+// *s_csum); every minor of A' is 2^(sum c - c_l) times that of A.  The sweep
+// takes 2^(-sum c) into its term exponents and the finishing kernel
+// multiplies column l by 2^(c_l); the range check is on A itself.
 template <bool CPLX>
 __device__ void grad_stage(const double* __restrict__ A, int n, int NR, typename Val<CPLX>::Y* D,
                            typename Val<CPLX>::Y* base, int* s_scale, uint32_t* s_flags, int* s_sall,
-                           uint32_t* gflags) {
+                           uint32_t* gflags, int* s_cexp, int* s_csum) {
   using Y = typename Val<CPLX>::Y;
   __shared__ int s_bound, s_zc, s_zi;
   const int tid = threadIdx.x;
+  const int csum = column_scales<CPLX ? 2 : 1>(A, n, s_cexp, true);
+  if (tid == 0) *s_csum = csum;
   if (tid == 0) {
     *s_flags = 0u;
     *s_sall = 0;
@@ -269,7 +277,7 @@ __device__ void grad_stage(const double* __restrict__ A, int n, int NR, typename
     for (int j = 0; j < n * W; ++j) {
       const double v = row[j];
       fin &= isfinite(v) ? 1 : 0;
-      absum += fabs(v);
+      absum += ldexp(fabs(v), s_cexp[j / W]);
     }
     int k = 0;
     if (fin && absum > 0.0) frexp(absum, &k);
@@ -278,26 +286,26 @@ __device__ void grad_stage(const double* __restrict__ A, int n, int NR, typename
       s = 60 - k;
       long long sr = 0, si = 0;
       for (int j = 0; j < n - 1; ++j) {
-        const long long qr = fin ? __double2ll_rn(ldexp(row[2 * j], s)) : 0;
-        const long long qi = fin ? __double2ll_rn(ldexp(row[2 * j + 1], s)) : 0;
+        const long long qr = fin ? __double2ll_rn(ldexp(row[2 * j], s + s_cexp[j])) : 0;
+        const long long qi = fin ? __double2ll_rn(ldexp(row[2 * j + 1], s + s_cexp[j])) : 0;
         sr += qr;
         si += qi;
         D[(2 * j) * NR + tid] = make_longlong2(2 * qr, 2 * qi);
         D[(2 * j + 1) * NR + tid] = make_longlong2(-2 * qr, -2 * qi);
       }
-      const long long nr = fin ? __double2ll_rn(ldexp(row[2 * (n - 1)], s)) : 0;
-      const long long ni = fin ? __double2ll_rn(ldexp(row[2 * (n - 1) + 1], s)) : 0;
+      const long long nr = fin ? __double2ll_rn(ldexp(row[2 * (n - 1)], s + s_cexp[n - 1])) : 0;
+      const long long ni = fin ? __double2ll_rn(ldexp(row[2 * (n - 1) + 1], s + s_cexp[n - 1])) : 0;
       base[tid] = make_longlong2(nr - sr, ni - si);
     } else {
       s = 61 - k;
       long long qsum = 0;
       for (int j = 0; j < n - 1; ++j) {
-        const long long q = fin ? __double2ll_rn(ldexp(row[j], s - 1)) : 0;
+        const long long q = fin ? __double2ll_rn(ldexp(row[j], s - 1 + s_cexp[j])) : 0;
         qsum += 2 * q;
         D[(2 * j) * NR + tid] = 4 * q;
         D[(2 * j + 1) * NR + tid] = -4 * q;
       }
-      const long long qn = fin ? 2 * __double2ll_rd(ldexp(row[n - 1], s - 1)) + 1 : 1;
+      const long long qn = fin ? 2 * __double2ll_rd(ldexp(row[n - 1], s - 1 + s_cexp[n - 1])) + 1 : 1;
       base[tid] = qn - qsum;
     }
     s_scale[tid] = s;
@@ -322,7 +330,7 @@ __device__ void grad_stage(const double* __restrict__ A, int n, int NR, typename
   __syncthreads();
   if (tid == 0) {
     uint32_t f = *s_flags;
-    if (s_bound + n > 1000) f |= 2u;
+    if (s_bound - csum + n > 1000) f |= 2u;
     f |= (uint32_t)min(s_zc, 255) << 8;
     f |= (uint32_t)s_zi << 16;
     *s_flags = f;
@@ -341,9 +349,9 @@ __global__ void __launch_bounds__(kGThreads, (CPLX && R == 4) ? 2 : 4) ryser_gra
   using Acc = typename V::Acc;
   constexpr int NR = kGL * R;
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ int s_scale[32];
+  __shared__ int s_scale[32], s_cexp[64];
   __shared__ uint32_t s_flags;
-  __shared__ int s_sall;
+  __shared__ int s_sall, s_csum;
   const int n = a.n, cq = a.cq;
   Y* D = reinterpret_cast<Y*>(smem);
   Y* base = D + (size_t)2 * (n > 1 ? n - 1 : 0) * NR;
@@ -381,14 +389,17 @@ __global__ void __launch_bounds__(kGThreads, (CPLX && R == 4) ? 2 : 4) ryser_gra
     const uint32_t q = (uint32_t)(bi - p * a.bipm);
     if (p != staged) {
       __syncthreads();
-      grad_stage<CPLX>(a.A + p * (uint64_t)n * n * W, n, NR, D, base, s_scale, &s_flags, &s_sall, a.flags + p);
+      grad_stage<CPLX>(a.A + p * (uint64_t)n * n * W, n, NR, D, base, s_scale, &s_flags, &s_sall, a.flags + p,
+                       s_cexp, &s_csum);
       staged = p;
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const int i = row0 + r;
-        eoff[r] = i < n ? -(s_sall - (s_scale[i] + 1)) : kDead;
+        eoff[r] = i < n ? -(s_sall + s_csum - (s_scale[i] + 1)) : kDead;
       }
     }
+    // the matrix's column scales, for the finishing kernel (once per matrix)
+    if (q == 0 && tid <= n) a.cs[p * kCsStride + tid] = tid < n ? s_cexp[tid] : s_csum;
     if (s_flags & 3u) continue;  // the finishing kernels write NaN
     const uint32_t qq = q * 16u + (uint32_t)sgi;
     const bool active = qq < a.qc;
@@ -539,6 +550,7 @@ struct FinishArgs {
   double* G;
   double* out;
   uint32_t* status_bits;  // [0]: EINVAL / ERANGE bits, [1]: the sweep's stop bits
+  const int* cs;          // GradArgs::cs
 };
 
 // G for column j of matrix p (grid: count x n, 256 threads): warp w sums slots
@@ -585,6 +597,9 @@ __global__ void __launch_bounds__(256) grad_finish_kernel(FinishArgs f) {
       const dd d = dd_add(dd{2.0 * U.hi, 2.0 * U.lo}, dd{-T.hi, -T.lo});
       g = sg * (d.hi + d.lo);
     }
+    // undo the column scales: the sweep summed 2^(-sum c) G'_kj, and
+    // G_kj = 2^(c_j - sum c) G'_kj (exact unless it underflows)
+    g = ldexp(g, f.cs[p * kCsStride + j]);
     if ((fl & 3u) || f.status_bits[1]) g = nan;
     else if (zc >= 2 || (zc == 1 && lane != zi)) g = 0.0;
     f.G[((size_t)p * n * n + (size_t)lane * n + j) * W + c] = g;
@@ -797,7 +812,8 @@ int grad_configure(int n, int count, bool cplx, GradCfg& g) {
   g.grid = (int)(g.nbi < B_full ? g.nbi : B_full);
   g.sb = g.bipm < (uint32_t)g.grid ? g.bipm : (uint32_t)g.grid;
   g.slot_doubles = (size_t)count * g.sb * n * NR * W;
-  g.ws_bytes = sizeof(double) * g.slot_doubles + sizeof(uint32_t) * ((size_t)count + 4);
+  g.ws_bytes = sizeof(double) * g.slot_doubles + sizeof(uint32_t) * ((size_t)count + 4) +
+               sizeof(int) * (size_t)count * kCsStride;
   g.smem = grad_smem(cplx, n, g.R, cq);
   return PERM_OK;
 }
@@ -808,6 +824,7 @@ int grad_launch(const GradCfg& g, const void* A, void* out, void* G, int32_t* st
   double* slots = static_cast<double*>(ws);
   uint32_t* flags = reinterpret_cast<uint32_t*>(slots + g.slot_doubles);
   uint32_t* bits = flags + g.count;
+  int* cs = reinterpret_cast<int*>(bits + 4);
   if (cudaMemsetAsync(ws, 0, g.ws_bytes, s) != cudaSuccess) {
     cudaGetLastError();
     return PERM_ECUDA;
@@ -826,6 +843,7 @@ int grad_launch(const GradCfg& g, const void* A, void* out, void* G, int32_t* st
   ga.abort_word = current_abort_word();
   ga.budget_ns = current_time_budget();
   ga.stopped = bits + 1;
+  ga.cs = cs;
   void* params[] = {&ga};
   cudaError_t e =
       cudaLaunchKernel(reinterpret_cast<const void*>(g.fn), dim3(g.grid), dim3(kGThreads), params, g.smem, s);
@@ -841,6 +859,7 @@ int grad_launch(const GradCfg& g, const void* A, void* out, void* G, int32_t* st
   fa.G = static_cast<double*>(G);
   fa.out = static_cast<double*>(out);
   fa.status_bits = bits;
+  fa.cs = cs;
   if (e == cudaSuccess) {
     if (g.cplx)
       grad_finish_kernel<true><<<dim3(g.count, g.n), 256, 0, s>>>(fa);

@@ -111,6 +111,10 @@ def test_time_budget_stops_every_sweep(pg):
         with pytest.raises(pg.PermError) as e:
             pg.perm_grad_batched(B)
         assert e.value.code == pg.PERM_ETIMEOUT
+        # a single real gradient
+        with pytest.raises(pg.PermError) as e:
+            pg.perm_grad(_dev(syn.signed_real(28, 50)))
+        assert e.value.code == pg.PERM_ETIMEOUT
     finally:
         pg.set_time_budget(None)
     # without the budget the same launches complete (the plan is replayed
@@ -139,6 +143,9 @@ def test_abort_word_stops_batched_and_gradient(pg, oracle):
         assert e.value.code == pg.PERM_EABORTED
         with pytest.raises(pg.PermError) as e:
             pg.perm_grad_batched(B)
+        assert e.value.code == pg.PERM_EABORTED
+        with pytest.raises(pg.PermError) as e:
+            pg.perm_grad(_dev(syn.signed_real(20, 49)))
         assert e.value.code == pg.PERM_EABORTED
         w.clear()
         res = plan.run()

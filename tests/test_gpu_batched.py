@@ -284,3 +284,45 @@ def test_large_k_chunked_vs_oracle_every_order(pg, oracle):
         ulp = 2.0 ** -52 * abs(want)
         assert abs(a - want) <= np.sqrt(2) * tol_a + ulp, (k, a, want, tol_a)
         assert abs(b - want) <= np.sqrt(2) * max(tol_a, tol_t) + ulp, (k, b, want, tol_t)
+
+
+def test_lines_scaled_far_apart(pg, oracle):
+    """perm(diag(r) A diag(d)) = perm(A) prod r prod d exactly: columns (and,
+    for row-labelled plans, label groups of rows) scaled by powers of two far
+    apart must give the unscaled oracle value times the factor, to the accuracy
+    of the unscaled matrix (exact equilibration of the toggled lines)."""
+    import math
+
+    g = syn.rng(2400)
+    ks = [8, 11, 14, 17, 20]
+    cexp = {k: np.zeros(k, dtype=int) for k in ks}
+    for k in ks:
+        cexp[k][[1, 4, k - 3, k - 1]] = [-300, 300, -290, 40]
+    # plain complex and real plans: columns scaled
+    cm = [syn.haar_unitary(k, 2401 + k) for k in ks]
+    rm = [syn.signed_real(k, 2420 + k) for k in ks]
+    got_c = pg.BatchPlan([m * np.ldexp(1.0, cexp[m.shape[0]]) for m in cm]).run()
+    got_r = pg.BatchPlan([m * np.ldexp(1.0, cexp[m.shape[0]]) for m in rm], dtype="float64").run()
+    for m, v in zip(cm, got_c):
+        e = int(cexp[m.shape[0]].sum())
+        assert abs(complex(math.ldexp(v.real, -e), math.ldexp(v.imag, -e)) - oracle.perm_dp_c128(m)) <= 1e-13
+    for m, v in zip(rm, got_r):
+        e = int(cexp[m.shape[0]].sum())
+        assert abs(math.ldexp(float(v), -e) - oracle.perm_f64(m)) <= 1e-12 * oracle.perm_f64(np.abs(m))
+    # row-labelled plans (the repeated-row sweeps toggle rows): each label's
+    # rows scaled alike
+    lm, ll, lf = [], [], []
+    for k in ks:
+        lab = np.sort(g.integers(0, k // 2, size=k)).astype(np.int32)
+        U = syn.haar_unitary(k, 2440 + k)
+        while True:  # rows far apart, their product within the binary64 range
+            re = g.integers(-280, 280, size=k)
+            rexp = re[lab]
+            if abs(int(rexp.sum())) <= 150:
+                break
+        lm.append((U[lab], U[lab] * np.ldexp(1.0, rexp)[:, None]))
+        ll.append(lab)
+        lf.append(int(rexp.sum()))
+    got_l = pg.BatchPlan([s for _, s in lm], row_labels=ll).run()
+    for (m, _), e, v in zip(lm, lf, got_l):
+        assert abs(complex(math.ldexp(v.real, -e), math.ldexp(v.imag, -e)) - oracle.perm_dp_c128(m)) <= 1e-12

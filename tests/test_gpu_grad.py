@@ -160,6 +160,82 @@ def test_zero_rows_and_bad_input(pg, oracle):
         pg.perm_grad(_dev(B))
 
 
+@pytest.mark.parametrize("n", [14, 15, 18, 21, 24, 26])
+def test_single_real_orders_14_to_26(pg, oracle, n):
+    """One real matrix of each order (R = 2, 3, 4 rows per lane): sampled
+    minors against the oracle, perm against the oracle, and the row expansion."""
+    A = syn.signed_real(n, 10500 + n)
+    p, G = pg.perm_grad(_dev(A))
+    G = G.cpu().numpy()
+    picks = (0, n // 3, n - 2, n - 1)
+    _check_minors(G, A, oracle, rows=picks if n > 18 else None, cols=picks if n > 18 else None)
+    assert abs(p - oracle.perm_f64(A)) <= 1e-10 * oracle.perm_f64(np.abs(A))
+    for i in range(n):
+        assert abs(float(np.dot(A[i], G[i])) - p) <= 1e-9 * float(np.sum(np.abs(A[i] * G[i])))
+
+
+def test_single_real_edge_cases(pg, oracle):
+    # a zero row (its Y stays 0: every product but its own minor vanishes),
+    # entries of very different size, and a nonfinite entry
+    A = syn.signed_real(15, 10600)
+    A[6] = 0.0
+    p, G = pg.perm_grad(_dev(A))
+    G = G.cpu().numpy()
+    assert p == 0.0
+    assert np.all(G[np.arange(15) != 6] == 0.0)
+    for l in (0, 7, 14):
+        assert abs(G[6, l] - oracle.perm_f64(_minor(A, 6, l))) <= 1e-11 * oracle.perm_f64(np.abs(_minor(A, 6, l)))
+    # perm is multilinear in rows and columns: a row times 2^300 and a column
+    # times 2^-200 scale every minor by an exact power of two, so the
+    # references come from the unscaled matrix B0
+    B0 = syn.signed_real(16, 10601)
+    B = B0.copy()
+    B[3] *= 2.0 ** 300
+    B[:, 5] *= 2.0 ** -200
+    p, G = pg.perm_grad(_dev(B))
+    G = G.cpu().numpy()
+    assert abs(p - math.ldexp(oracle.perm_f64(B0), 100)) <= math.ldexp(1e-10 * oracle.perm_f64(np.abs(B0)), 100)
+    for k, l in ((3, 5), (0, 0), (3, 0), (15, 5)):
+        M = _minor(B0, k, l)
+        e = (300 if k != 3 else 0) - (200 if l != 5 else 0)
+        err = abs(G[k, l] - math.ldexp(oracle.perm_f64(M), e))
+        assert err <= math.ldexp(1e-10 * oracle.perm_f64(np.abs(M)), e), (k, l)
+    B[2, 9] = np.inf
+    with pytest.raises(pg.PermError) as e:
+        pg.perm_grad(_dev(B))
+    assert e.value.code == pg.PERM_EINVAL
+
+
+def test_gradient_columns_scaled_far_apart(pg, oracle):
+    """Columns scaled by 2^-300 .. 2^300, real (one matrix and a batch) and
+    complex: every minor is the unscaled oracle minor times an exact power of
+    two (the sweep equilibrates the columns and scales G back)."""
+    n = 12
+    ce = np.zeros(n, dtype=int)
+    ce[[1, 4, 8, 11]] = [-300, 300, -290, 40]
+    d = np.ldexp(1.0, ce)
+    for A0, cplx in ((syn.signed_real(n, 10700), False), (syn.haar_unitary(n, 10701), True)):
+        p, G = pg.perm_grad(_dev(A0 * d))
+        G = G.cpu().numpy()
+        want_p = oracle.perm_c128(A0) if cplx else oracle.perm_f64(A0)
+        assert abs(p * 2.0 ** -int(ce.sum()) - want_p) <= 1e-12 * oracle.perm_f64(np.abs(A0))
+        for k in range(n):
+            for l in range(n):
+                M = _minor(A0, k, l)
+                e = int(ce.sum() - ce[l])
+                want = oracle.perm_c128(M) if cplx else oracle.perm_f64(M)
+                err = abs(G[k, l] * 2.0 ** -e - want)
+                assert err <= 1e-12 * oracle.perm_f64(np.abs(M)), (cplx, k, l, err)
+    B = np.stack([syn.signed_real(n, 10710 + i) for i in range(5)])
+    p, G = pg.perm_grad_batched(_dev(B * d))
+    G = G.cpu().numpy()
+    for i in range(5):
+        for k, l in ((0, 1), (3, 4), (11, 0), (6, 11)):
+            M = _minor(B[i], k, l)
+            e = int(ce.sum() - ce[l])
+            assert abs(G[i, k, l] * 2.0 ** -e - oracle.perm_f64(M)) <= 1e-12 * oracle.perm_f64(np.abs(M)), (i, k, l)
+
+
 def test_row_expansion_identity(pg):
     for n, seed in ((9, 1), (16, 2), (23, 3), (32, 4)):
         A = syn.signed_real(n, 11000 + seed)
