@@ -53,7 +53,7 @@ constexpr int kGWarps = 4;              // warps per CTA
 constexpr int kGThreads = 32 * kGWarps;
 constexpr int kGSub = kGWarps * 4;      // sub-groups per CTA
 constexpr int kDead = -1000000;         // exponent offset of rows that contribute nothing
-constexpr int kCsStride = 33;           // ints per matrix in GradArgs::cs (n <= 32, plus the sum)
+constexpr int kCsStride = 32;           // ints per matrix in GradArgs::cs (n <= 32)
 
 struct GradArgs {
   const double* A;    // count matrices, n*n scalars each (a scalar is 1 or 2 doubles)
@@ -68,7 +68,7 @@ struct GradArgs {
   const volatile uint32_t* abort_word;  // perm_set_abort_word (device view), or null
   uint64_t budget_ns;                   // perm_set_time_budget, 0: none
   uint32_t* stopped;                    // bit 0: aborted, bit 1: out of time (zeroed)
-  int* cs;            // [count][kCsStride]: column scales c_0..c_{n-1}, then their sum
+  int* cs;            // [count][kCsStride]: column scales c_0..c_{n-1}
 };
 
 // ------------------------------------------------------------ real values
@@ -399,7 +399,7 @@ __global__ void __launch_bounds__(kGThreads, (CPLX && R == 4) ? 2 : 4) ryser_gra
       }
     }
     // the matrix's column scales, for the finishing kernel (once per matrix)
-    if (q == 0 && tid <= n) a.cs[p * kCsStride + tid] = tid < n ? s_cexp[tid] : s_csum;
+    if (q == 0 && tid < n) a.cs[p * kCsStride + tid] = s_cexp[tid];
     if (s_flags & 3u) continue;  // the finishing kernels write NaN
     const uint32_t qq = q * 16u + (uint32_t)sgi;
     const bool active = qq < a.qc;
