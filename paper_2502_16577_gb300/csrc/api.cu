@@ -5,7 +5,9 @@
 #include <string.h>
 
 #include <atomic>
+#include <map>
 #include <mutex>
+#include <tuple>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -35,16 +37,25 @@ static int current_device_facts(DeviceFacts& f) {
   return PERM_OK;
 }
 
-// Blocks per SM of a kernel (after raising its dynamic shared-memory limit).
+// Blocks per SM of a kernel (after raising its dynamic shared-memory limit),
+// queried once per device, kernel and shared-memory size instead of on every
+// launch.
 static int blocks_per_sm(const KernelEntry& ke) {
   static std::mutex mu;
+  static std::map<std::tuple<int, const void*, size_t>, int> cache;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+  const auto key = std::make_tuple(dev, ke.fn, ke.smem);
   std::lock_guard<std::mutex> lock(mu);
+  const auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
   if (ke.smem > 48 * 1024) {
     if (cudaFuncSetAttribute(ke.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ke.smem) != cudaSuccess)
       return -1;
   }
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, ke.fn, kBlock, ke.smem) != cudaSuccess) return -1;
+  if (nb > 0) cache.emplace(key, nb);
   return nb;
 }
 
