@@ -183,7 +183,10 @@ int perm_sparse_range(int n, const int32_t* cptrs, const int32_t* rids, const do
  * kernel that pops work items (32 matrices of one size per warp for short
  * sweeps, 32 aligned Gray chunks of one matrix per warp for long ones,
  * longest first) from an atomic counter, and a finish kernel that adds each
- * matrix's item partials in a fixed order.
+ * matrix's item partials in a fixed order.  The prep kernel equilibrates the
+ * lines a unit's sweep toggles as perm() does (columns; for the repeated-row
+ * sweeps of a labelled plan, the rows, equal rows alike) and takes the scale
+ * back out of the result exactly.
  *
  * perm_batched_plan_create - build a plan (host call; allocates the plan's
  *   device buffers and captures the graph; synchronous).
@@ -259,7 +262,9 @@ void perm_batched_plan_destroy(perm_batch_plan* plan);
  * accumulated with per-chunk running prefixes so each step costs O(n)
  * additions.  The paper has no gradient; the sweep and its chunking are those
  * of Alg. 1 / Alg. 3.  The permanent is returned through the row expansion
- * perm = sum_l a_0l G_0l (its error follows G's, not perm()'s).
+ * perm = sum_l a_0l G_0l (its error follows G's, not perm()'s).  Columns are
+ * equilibrated as in perm(); since every minor of A D is det D / d_l times
+ * that of A, G is scaled back column by column, exactly.
  *   type    PERM_F64 or PERM_C128 (interleaved re, im); 0 <= n <= 32.
  *   A       device, n*n elements row-major;  out device, one element;
  *   G       device, n*n elements row-major (the holomorphic derivative for
