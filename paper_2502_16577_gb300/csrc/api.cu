@@ -145,7 +145,6 @@ static int launch_ryser(const KernelEntry& ke, const void* A, int n, uint64_t g_
   args.n = n;
   args.c = c;
   args.mode = mode;
-  args.one = 1;
   args.g_begin = g_begin;
   args.g_end = g_end;
   args.k_begin = k_begin;

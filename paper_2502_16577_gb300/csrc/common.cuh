@@ -87,7 +87,6 @@ struct RyserArgs {
   int n;
   int c;              // log2 of the chunk length, 0..30
   int mode;           // 0: write the finished permanent, 1: write the raw range sum
-  int one;            // always 1 (a multiplier the compiler cannot fold away)
   uint64_t g_begin, g_end;
   uint64_t k_begin, nchunks;
   void* part;         // per-CTA partials (scratch, gridDim.x entries)

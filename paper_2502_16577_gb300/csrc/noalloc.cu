@@ -97,7 +97,6 @@ extern "C" int perm_f64_noalloc(const double* A, int n, double* out, int32_t* st
   args.n = n;
   args.c = c;
   args.mode = 0;
-  args.one = 1;
   args.g_begin = 0;
   args.g_end = N;
   args.k_begin = 0;

@@ -441,7 +441,6 @@ static int sparse_launch(int n, const int32_t* cptrs, const int32_t* rids, const
   args.n = n;
   args.nnz = (int)nnz;
   args.c = c;
-  args.one = 1;
   args.mode = mode;
   args.paper_order = paper_order;
   args.g_begin = g0;
