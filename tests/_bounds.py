@@ -23,7 +23,9 @@ Dense real kernel (62-bit products of exact fixed-point rows):
   product: v = M A / 2^64 with M >= 2^62 loses less than 1.5 units of v,
          i.e. at most 6 units of A = |Y_i|: |dx_i| <= 3 R_i 2^-60; counted as
          R_i 2^-58, which also covers a chain whose mantissa fell below 2^62
-         after a factor with |Y_i| < 2^34;
+         after a factor with |Y_i| < 2^34 (a factor |Y_i| = 1, where x_i is 0
+         before the odd rounding, empties the chain; tests/test_bounds.py
+         checks such sweeps bit for bit against this bound);
   merge of the two chains: relative 1.5 2^-60; head/tail split: exact;
   double-double accumulation: below 2^-64 S for chunks of at most 2^20 steps.
   => |delta| <= 2 [(2^-58 + (1 + n_g) 2^-61) W + 2^-59 S]   (factor 2: second
