@@ -9,6 +9,10 @@ rational arithmetic:
   W are computed with Fractions (every binary64 entry is a dyadic rational);
 * the double-double oracle (ryser_dd_stats_range) must lie within
   dd_oracle_bound of the exact sum and reproduce S and W;
+* the same for the complex double-double oracle (ryser_cdd_range) and a
+  bit-level model of the one-lane complex sweep (n < 16: signed 62-bit limb
+  products, the larger part renormalised to 2^60, two chains and a merge)
+  against complex_sweep_bound, part by part;
 * a bit-level model of the dense real sweep's fixed-point arithmetic (the
   staging of every row, the odd last column, the 62-bit products with their
   renormalising shifts, the exponent bookkeeping, and the integer assembly of
@@ -27,7 +31,7 @@ import numpy as np
 import pytest
 
 import synthetic as syn
-from _bounds import dd_oracle_bound, real_rows_on_grid, real_sweep_bound
+from _bounds import complex_sweep_bound, dd_oracle_bound, real_rows_on_grid, real_sweep_bound
 
 M32 = (1 << 32) - 1
 
@@ -208,3 +212,148 @@ def test_grid_detection():
     assert real_rows_on_grid(np.array([[1.0, -2.0], [0.5, 0.25]]))
     assert not real_rows_on_grid(np.array([[2.0 ** -70, 1.0], [1.0, 1.0]]))
     assert real_rows_on_grid(np.array([[1.0, 2.0 ** -70], [1.0, 1.0]]))
+
+
+# ---------------------------------------------------------------- complex
+
+
+def _s32(v):
+    v &= M32
+    return v - (1 << 32) if v >> 31 else v
+
+
+def _split62(y):
+    """(bits 31..62 of y as a signed 32-bit limb, bits 0..30)."""
+    u = y & ((1 << 64) - 1)
+    ul, uh = u & M32, u >> 32
+    return _s32((uh << 1) | (ul >> 31)), ul & 0x7FFFFFFF
+
+
+def _cprod_mul(p, yr, yi):
+    """The complex limb product step: the middle partial products (scale 2^31,
+    floored by an arithmetic shift), the high ones (scale 2^62), then both
+    parts shifted so that the larger one's top bit sits at 2^60 (the top bit
+    found in the ones'-complement magnitudes of the high words).  p = [r1, r0,
+    i1, i0]; returns the shift s (the product was scaled by 2^(s - 62))."""
+    r1, r0, i1, i0 = p
+    yr1, yr0 = _split62(yr)
+    yi1, yi0 = _split62(yi)
+    ni1, ni0 = _s32(-i1), _s32(-i0)
+    tr = (r1 * yr0 + r0 * yr1 + ni1 * yi0 + ni0 * yi1) >> 31
+    ti = (r1 * yi0 + r0 * yi1 + i1 * yr0 + i0 * yr1) >> 31
+    vr = r1 * yr1 + ni1 * yi1 + tr
+    vi = r1 * yi1 + i1 * yr1 + ti
+    w = 0
+    for v in (vr, vi):
+        h = _s32(v >> 32)
+        w |= (h ^ (h >> 31)) & M32
+    pos = w.bit_length() - 1 if w else -1
+    sh = 28 - pos
+    assert 0 <= sh < 64
+    out = []
+    for v in (vr, vi):
+        u = (v << sh) & ((1 << 64) - 1)
+        out.extend(_split62(u - (1 << 64) if u >> 63 else u))
+    p[:] = out
+    return sh
+
+
+def _model_cplx_sweep(A):
+    """The one-lane complex sweep's range sum (re, im) from its integer
+    arithmetic: rows s_i = 60 - k_i with k_i from sum_j |re| + |im|, every
+    entry rounded to nearest, two chains over even / odd rows starting at 2^60,
+    their merge, and the term z 2^(ebase - sum of the shifts) (its exact
+    head + tail)."""
+    n = A.shape[0]
+    Q, ssum = [], 0
+    for i in range(n):
+        absum = 0.0
+        for j in range(n):
+            absum += abs(float(A[i, j].real))
+            absum += abs(float(A[i, j].imag))
+        k = math.frexp(absum)[1] if absum > 0 else 0
+        s = 60 - k
+        ssum += s
+        Q.append([(round(Fraction(float(A[i, j].real)) * Fraction(2) ** s),
+                   round(Fraction(float(A[i, j].imag)) * Fraction(2) ** s)) for j in range(n)])
+    Yr = [Q[i][n - 1][0] - sum(q[0] for q in Q[i][:n - 1]) for i in range(n)]
+    Yi = [Q[i][n - 1][1] - sum(q[1] for q in Q[i][:n - 1]) for i in range(n)]
+    ebase = 62 * (n + 1) - 120 - ssum - n
+    tot_r, tot_i = Fraction(0), Fraction(0)
+    for g in range(1 << (n - 1)):
+        if g:
+            j = (g & -g).bit_length() - 1
+            sgn = -1 if (g >> (j + 1)) & 1 else 1
+            for i in range(n):
+                Yr[i] += 2 * sgn * Q[i][j][0]
+                Yi[i] += 2 * sgn * Q[i][j][1]
+        chains = [[1 << 29, 0, 0, 0], [1 << 29, 0, 0, 0]]  # 2^60 each
+        shifts = 0
+        for i in range(n):
+            assert abs(Yr[i]) < (1 << 61) and abs(Yi[i]) < (1 << 61)
+            shifts += _cprod_mul(chains[i & 1], Yr[i], Yi[i])
+        b = chains[1]
+        shifts += _cprod_mul(chains[0], b[0] * (1 << 31) + b[1], b[2] * (1 << 31) + b[3])
+        a = chains[0]
+        scale = Fraction(2) ** (ebase - shifts) * (-1 if g & 1 else 1)
+        tot_r += (a[0] * (1 << 31) + a[1]) * scale
+        tot_i += (a[2] * (1 << 31) + a[3]) * scale
+    return tot_r, tot_i
+
+
+def _exact_cplx(A):
+    """Exact complex range sum (re, im) as Fractions, and S, W in binary64."""
+    n = A.shape[0]
+    F = [[(Fraction(float(v.real)), Fraction(float(v.imag))) for v in row] for row in A]
+    xr = [(F[i][n - 1][0] - sum(v[0] for v in F[i][:n - 1])) / 2 for i in range(n)]
+    xi = [(F[i][n - 1][1] - sum(v[1] for v in F[i][:n - 1])) / 2 for i in range(n)]
+    R = [float(np.sum(np.abs(A[i]))) for i in range(n)]
+    tr, ti, S, W = Fraction(0), Fraction(0), 0.0, 0.0
+    for g in range(1 << (n - 1)):
+        if g:
+            j = (g & -g).bit_length() - 1
+            enter = not ((g >> (j + 1)) & 1)
+            for i in range(n):
+                xr[i] += F[i][j][0] if enter else -F[i][j][0]
+                xi[i] += F[i][j][1] if enter else -F[i][j][1]
+        pr, pi = Fraction(1), Fraction(0)
+        for a, b in zip(xr, xi):
+            pr, pi = pr * a - pi * b, pr * b + pi * a
+        if g & 1:
+            pr, pi = -pr, -pi
+        tr += pr
+        ti += pi
+        mods = [math.hypot(float(a), float(b)) for a, b in zip(xr, xi)]
+        S += math.prod(mods)
+        for i in range(n):
+            W += R[i] * math.prod(m for k, m in enumerate(mods) if k != i)
+    return tr, ti, S, W
+
+
+def _cplx_cases():
+    g = syn.rng(9200)
+    out = [("Haar n=8", syn.haar_unitary(8, 9201)),
+           ("Gaussian n=9", (g.standard_normal((9, 9)) + 1j * g.standard_normal((9, 9))) / math.sqrt(2.0)),
+           ("Gaussian integers n=8", (g.integers(-2, 3, size=(8, 8)) + 1j * g.integers(-2, 3, size=(8, 8))))]
+    C = syn.haar_unitary(8, 9202)
+    C[3] = 0.0
+    C[3, 0], C[3, 1] = 0.5 + 0.5j, -0.5 - 0.5j  # x_3 = 0 on half the steps
+    out.append(("x_3 = 0 on half the steps n=8", C))
+    return out
+
+
+@pytest.mark.parametrize("name,A", _cplx_cases(), ids=lambda v: v if isinstance(v, str) else "")
+def test_complex_oracle_and_model_sweep_within_their_bounds(oracle, name, A):
+    A = np.ascontiguousarray(A, dtype=np.complex128)
+    n = A.shape[0]
+    er, ei, S, W = _exact_cplx(A)
+    r = oracle.ryser_cdd_range(A, 0, 1 << (n - 1))
+    tol_dd = Fraction(dd_oracle_bound(S, n))
+    assert abs(Fraction(r["re_hi"]) + Fraction(r["re_lo"]) - er) <= tol_dd, name
+    assert abs(Fraction(r["im_hi"]) + Fraction(r["im_lo"]) - ei) <= tol_dd, name
+    assert r["S"] == pytest.approx(S, rel=1e-12)
+    assert r["W"] == pytest.approx(W, rel=1e-12)
+    mr, mi = _model_cplx_sweep(A)
+    bound = Fraction(complex_sweep_bound(S, W, n))
+    assert abs(mr - er) <= bound and abs(mi - ei) <= bound, (name, float(abs(mr - er)), float(abs(mi - ei)),
+                                                             float(bound))
