@@ -49,7 +49,6 @@ struct SpArgs {
   int n;
   int nnz;
   int c;
-  int one;
   int mode;         // 0: write the finished permanent, 1: write the raw range sum (hi, lo)
   int paper_order;  // 1: Alg. 2's own column order (no quiet-row reordering)
   uint64_t g_begin, g_end;  // accumulated steps
