@@ -13,6 +13,9 @@ rational arithmetic:
   bit-level model of the one-lane complex sweep (n < 16: signed 62-bit limb
   products, the larger part renormalised to 2^60, two chains and a merge)
   against complex_sweep_bound, part by part;
+* a bit-level model of the sparse sweep in Alg. 2's column order (rows
+  without the odd unit, exact zeros skipped, the product of all rows merged
+  with two empty chains) against the same real_sweep_bound;
 * a bit-level model of the dense real sweep's fixed-point arithmetic (the
   staging of every row, the odd last column, the 62-bit products with their
   renormalising shifts, the exponent bookkeeping, and the integer assembly of
@@ -357,3 +360,69 @@ def test_complex_oracle_and_model_sweep_within_their_bounds(oracle, name, A):
     bound = Fraction(complex_sweep_bound(S, W, n))
     assert abs(mr - er) <= bound and abs(mi - ei) <= bound, (name, float(abs(mr - er)), float(abs(mi - ei)),
                                                              float(bound))
+
+
+# ----------------------------------------------------------------- sparse
+
+
+def _model_sparse_paper_order(A):
+    """The sparse sweep's range sum over all steps in Alg. 2's column order
+    (no column moved to the low Gray bits): rows s_i = 61 - k_i with every
+    stored entry rounded to nearest (no odd unit, so Y_i is 0 exactly when its
+    fixed-point sum is), a step whose rows include a zero adds nothing, else
+    the product of all rows in row order forms one chain that is merged into
+    two empty chains (2^62 each), and the term is assembled as in the dense
+    sweep."""
+    n = A.shape[0]
+    Q, ssum = [], 0
+    for i in range(n):
+        absum = 0.0
+        for j in range(n):
+            if A[i, j] != 0.0:
+                absum += abs(float(A[i, j]))
+        k = math.frexp(absum)[1] if absum > 0 else 0
+        s = 61 - k
+        ssum += s
+        Q.append([round(Fraction(float(A[i, j])) * Fraction(2) ** s) for j in range(n)])
+    Y = [Q[i][n - 1] - sum(Q[i][:n - 1]) for i in range(n)]
+    F0 = 33 * n + 966 - ssum
+    total = Fraction(0)
+    for g in range(1 << (n - 1)):
+        if g:
+            j = (g & -g).bit_length() - 1
+            sgn = -1 if (g >> (j + 1)) & 1 else 1
+            for i in range(n):
+                Y[i] += 2 * sgn * Q[i][j]
+        if any(y == 0 for y in Y):
+            continue
+        pq = [0, 1 << 30]
+        epos, neg = 0, 0
+        for y in Y:
+            a = abs(y)
+            neg ^= y < 0
+            pq[0], pq[1], pos = _prod_mul(pq[0], pq[1], a & M32, a >> 32)
+            epos += pos
+        m0, m1, pos = _prod_mul(0, 1 << 30, 0, 1 << 30)  # the two empty chains
+        epos += pos
+        m0, m1, pos = _prod_mul(m0, m1, pq[0], pq[1])
+        epos += pos
+        head, tail = _term_head_tail((m1 << 32) | m0, F0 + epos, int(neg ^ (g & 1)))
+        total += head + tail
+    return total
+
+
+def _sparse_cases():
+    return [("density 0.4 n=10", syn.sparse_real(10, 9301, 0.4)),
+            ("density 0.3 n=9", syn.sparse_real(9, 9302, 0.3)),
+            ("0/1 density 0.5 n=10 (exact zeros on many steps)",
+             (syn.rng(9303).random((10, 10)) < 0.5).astype(np.float64) + np.eye(10))]
+
+
+@pytest.mark.parametrize("name,A", _sparse_cases(), ids=lambda v: v if isinstance(v, str) else "")
+def test_sparse_model_sweep_within_the_real_bound(name, A):
+    n = A.shape[0]
+    exact, S, W = _exact(A)
+    model = _model_sparse_paper_order(A)
+    bound = real_sweep_bound(float(S), float(W), n, real_rows_on_grid(A))
+    err = abs(model - exact)
+    assert err <= Fraction(bound), (name, float(err), bound)
