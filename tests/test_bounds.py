@@ -16,6 +16,9 @@ rational arithmetic:
 * a bit-level model of the sparse sweep in Alg. 2's column order (rows
   without the odd unit, exact zeros skipped, the product of all rows merged
   with two empty chains) against the same real_sweep_bound;
+* a bit-level model of the real gradient sweep (normalised leaves, the
+  exclusive butterfly over eight lanes, one rounding per term, binary64
+  prefix and column sums per chunk) against the derived 2^-42 S_k;
 * a bit-level model of the dense real sweep's fixed-point arithmetic (the
   staging of every row, the odd last column, the 62-bit products with their
   renormalising shifts, the exponent bookkeeping, and the integer assembly of
@@ -426,3 +429,148 @@ def test_sparse_model_sweep_within_the_real_bound(name, A):
     bound = real_sweep_bound(float(S), float(W), n, real_rows_on_grid(A))
     err = abs(model - exact)
     assert err <= Fraction(bound), (name, float(err), bound)
+
+
+# --------------------------------------------------------------- gradient
+
+TOL_GRAD = 2.0 ** -42  # the gradient sweep's derived bound, relative to S_k
+
+
+def _leaf(y):
+    """|Y| normalised to a mantissa in [2^62, 2^63): (m0, m1, e), |Y| = M 2^e."""
+    a = abs(y)
+    lz = 64 - a.bit_length()
+    m = a << (lz - 1)
+    return [m & M32, m >> 32, 1 - lz]
+
+
+def _gmul(a, b):
+    m0, m1, pos = _prod_mul(a[0], a[1], b[0], b[1])
+    return [m0, m1, a[2] + b[2] + 34 + pos]
+
+
+def _to_double(v, eoff, neg):
+    """The term's single rounding: the top 53 of the mantissa's 63 bits
+    (+512 then a 10-bit shift, ties away from zero) placed on the exponent
+    field f = e + eoff + 62 + 1022, flushed to zero below the normal range."""
+    f = v[2] + eoff + 62 + 1022
+    if f < 1:
+        return 0.0
+    M = (v[1] << 32) | v[0]
+    word = (min(f, 2045) << 52) + ((M + 512) >> 10)
+    x = float(_f64_from_bits(word))
+    return -x if neg else x
+
+
+def _model_grad(A, cq):
+    """The real gradient sweep (8 lanes per chunk, two rows per lane, n <= 16)
+    from its arithmetic: fixed-point rows as in the forward sweep, normalised
+    leaves, the local exclusive products and the three-level exclusive
+    butterfly over the lanes, one rounding of every term to binary64, the
+    running prefix P_k and the column sums U_kj (j < cq) in binary64 inside
+    each chunk, the chunk-end additions of P as the kernel does them.  The
+    chunks' contributions are then added exactly.  Returns G (Fractions)."""
+    n = A.shape[0]
+    NR, L = 16, 8
+    Q, s_sc = [], []
+    for i in range(n):
+        absum = 0.0
+        for j in range(n):
+            absum += abs(float(A[i, j]))
+        k = math.frexp(absum)[1] if absum > 0 else 0
+        s = 61 - k
+        row = [2 * round(Fraction(float(A[i, j])) * Fraction(2) ** (s - 1)) for j in range(n - 1)]
+        row.append(2 * math.floor(Fraction(float(A[i, n - 1])) * Fraction(2) ** (s - 1)) + 1)
+        Q.append(row)
+        s_sc.append(s)
+    s_all = sum(s + 1 for s in s_sc)
+    eo = [-(s_all - (s_sc[i] + 1)) if i < n else None for i in range(NR)]
+    U = [[Fraction(0)] * n for _ in range(n)]  # U[k][l]
+    T = [Fraction(0)] * n
+    for c0 in range(0, 1 << (n - 1), 1 << cq):
+        G0 = c0 ^ (c0 >> 1)
+        Y = [sum((Q[i][j] if (j == n - 1 or (G0 >> j) & 1) else -Q[i][j]) for j in range(n)) if i < n else 1
+             for i in range(NR)]
+        P = [0.0] * n
+        Uc = [[0.0] * cq for _ in range(n)]
+        for t in range(1 << cq):
+            g = c0 + t
+            if t:
+                j = (t & -t).bit_length() - 1
+                leave = (g >> (j + 1)) & 1
+                for i in range(n):
+                    Y[i] += -2 * Q[i][j] if leave else 2 * Q[i][j]
+                for k in range(n):
+                    Uc[k][j] = Uc[k][j] + (P[k] if leave else -P[k])
+            lf = [_leaf(y) for y in Y]
+            negs = [1 if y < 0 else 0 for y in Y]
+            grp = [_gmul(lf[2 * l], lf[2 * l + 1]) for l in range(L)]
+            o = [grp[l ^ 1] for l in range(L)]
+            grp = [_gmul(grp[l], o[l]) for l in range(L)]
+            x2 = [grp[l ^ 2] for l in range(L)]
+            o = [_gmul(o[l], x2[l]) for l in range(L)]
+            grp = [_gmul(grp[l], x2[l]) for l in range(L)]
+            x4 = [grp[l ^ 4] for l in range(L)]
+            o = [_gmul(o[l], x4[l]) for l in range(L)]
+            allneg = sum(negs) & 1
+            for k in range(n):
+                l, r = divmod(k, 2)
+                v = _gmul(o[l], lf[2 * l + 1 - r])
+                neg = allneg ^ negs[k] ^ (g & 1)
+                P[k] = P[k] + _to_double(v, eo[k], neg)
+        G1 = (c0 + (1 << cq) - 1) ^ ((c0 + (1 << cq) - 1) >> 1)
+        for k in range(n):
+            T[k] += Fraction(P[k])
+            for j in range(n - 1):
+                if j < cq:
+                    U[k][j] += Fraction(Uc[k][j] + (P[k] if (G1 >> j) & 1 else 0.0))
+                elif (G0 >> j) & 1:
+                    U[k][j] += Fraction(P[k])
+    sg = -1 if (n - 1) & 1 else 1
+    return [[sg * (2 * U[k][l] - T[k]) if l < n - 1 else sg * T[k] for l in range(n)] for k in range(n)]
+
+
+def _exact_grad(A):
+    """Exact G_kl = (-1)^(n-1) sum_g (-1)^g delta_l(g) prod_{i != k} x_i(g) and
+    S_k = sum_g prod_{i != k} |x_i(g)|."""
+    n = A.shape[0]
+    F = [[Fraction(float(v)) for v in row] for row in A]
+    x = [(F[i][n - 1] - sum(F[i][:n - 1])) / 2 for i in range(n)]
+    G = [[Fraction(0)] * n for _ in range(n)]
+    S = [Fraction(0)] * n
+    sg = -1 if (n - 1) & 1 else 1
+    for g in range(1 << (n - 1)):
+        if g:
+            j = (g & -g).bit_length() - 1
+            enter = not ((g >> (j + 1)) & 1)
+            for i in range(n):
+                x[i] += F[i][j] if enter else -F[i][j]
+        gray = g ^ (g >> 1)
+        for k in range(n):
+            v = Fraction(1)
+            for i in range(n):
+                if i != k:
+                    v *= x[i]
+            S[k] += abs(v)
+            w = -v if g & 1 else v
+            for l in range(n):
+                d = 1 if (l == n - 1 or (gray >> l) & 1) else -1
+                G[k][l] += sg * d * w
+    return G, S
+
+
+@pytest.mark.parametrize("n,cq,seed", [(9, 4, 9401), (10, 5, 9402)])
+def test_gradient_model_within_its_bound(oracle, n, cq, seed):
+    A = syn.signed_real(n, seed)
+    G, S = _exact_grad(A)
+    # the exact sums are the minor permanents (a check of _exact_grad itself)
+    for k, l in ((0, 0), (n - 1, 2)):
+        M = np.delete(np.delete(A, k, axis=0), l, axis=1)
+        assert float(G[k][l]) == pytest.approx(oracle.perm_dp_f64(M), rel=1e-12, abs=1e-12)
+    Gm = _model_grad(A, cq)
+    worst = 0.0
+    for k in range(n):
+        for l in range(n):
+            r = float(abs(Gm[k][l] - G[k][l]) / S[k])
+            worst = max(worst, r)
+    assert worst <= TOL_GRAD, worst
