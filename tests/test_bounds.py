@@ -9,10 +9,11 @@ rational arithmetic:
   W are computed with Fractions (every binary64 entry is a dyadic rational);
 * the double-double oracle (ryser_dd_stats_range) must lie within
   dd_oracle_bound of the exact sum and reproduce S and W;
-* the same for the complex double-double oracle (ryser_cdd_range) and a
-  bit-level model of the one-lane complex sweep (n < 16: signed 62-bit limb
-  products, the larger part renormalised to 2^60, two chains and a merge)
-  against complex_sweep_bound, part by part;
+* the same for the complex double-double oracle (ryser_cdd_range) and
+  bit-level models of the complex sweeps (signed 62-bit limb products, the
+  larger part renormalised to 2^60): the one-lane layout (n < 16: two chains
+  and a merge) and the two-lane layout (n >= 16: one chain per lane over half
+  the rows, then a merge) against complex_sweep_bound, part by part;
 * a bit-level model of the sparse sweep in Alg. 2's column order (rows
   without the odd unit, exact zeros skipped, the product of all rows merged
   with two empty chains) against the same real_sweep_bound;
@@ -574,3 +575,61 @@ def test_gradient_model_within_its_bound(oracle, n, cq, seed):
             r = float(abs(Gm[k][l] - G[k][l]) / S[k])
             worst = max(worst, r)
     assert worst <= TOL_GRAD, worst
+
+
+def _model_cplx2_sweep(A):
+    """The two-lane complex sweep (used from n = 16): lane 0 multiplies rows
+    0..R-1 and lane 1 rows R..2R-1 into one chain each (R = ceil(n/2); an odd
+    n pads lane 1 with the constant 2^60, taken back out of the exponent), the
+    two halves are merged by one more limb product, and the term z 2^E is
+    added exactly.  The arithmetic does not depend on n, so small n check the
+    bound of the kernel's layout."""
+    n = A.shape[0]
+    R = (n + 1) // 2
+    Q, ssum = [], 0
+    for i in range(n):
+        absum = 0.0
+        for j in range(n):
+            absum += abs(float(A[i, j].real))
+            absum += abs(float(A[i, j].imag))
+        k = math.frexp(absum)[1] if absum > 0 else 0
+        s = 60 - k
+        ssum += s
+        Q.append([(round(Fraction(float(A[i, j].real)) * Fraction(2) ** s),
+                   round(Fraction(float(A[i, j].imag)) * Fraction(2) ** s)) for j in range(n)])
+    Yr = [Q[i][n - 1][0] - sum(q[0] for q in Q[i][:n - 1]) for i in range(n)] + [1 << 60] * (2 * R - n)
+    Yi = [Q[i][n - 1][1] - sum(q[1] for q in Q[i][:n - 1]) for i in range(n)] + [0] * (2 * R - n)
+    eoff = -(ssum + n) - (60 if n & 1 else 0)
+    tot_r, tot_i = Fraction(0), Fraction(0)
+    for g in range(1 << (n - 1)):
+        if g:
+            j = (g & -g).bit_length() - 1
+            sgn = -1 if (g >> (j + 1)) & 1 else 1
+            for i in range(n):
+                Yr[i] += 2 * sgn * Q[i][j][0]
+                Yi[i] += 2 * sgn * Q[i][j][1]
+        halves = []
+        for h in range(2):
+            p = [1 << 29, 0, 0, 0]
+            ss = 0
+            for r in range(R):
+                ss += _cprod_mul(p, Yr[h * R + r], Yi[h * R + r])
+            halves.append((p, -60 + 62 * R - ss))
+        (a, ea), (b, eb) = halves
+        s = _cprod_mul(a, b[0] * (1 << 31) + b[1], b[2] * (1 << 31) + b[3])
+        scale = Fraction(2) ** (ea + eb + 62 - s + eoff) * (-1 if g & 1 else 1)
+        tot_r += (a[0] * (1 << 31) + a[1]) * scale
+        tot_i += (a[2] * (1 << 31) + a[3]) * scale
+    return tot_r, tot_i
+
+
+@pytest.mark.parametrize("name,A", _cplx_cases()[:2] + [("Haar n=9 (a padded row)", syn.haar_unitary(9, 9203))],
+                         ids=lambda v: v if isinstance(v, str) else "")
+def test_two_lane_complex_model_within_the_bound(name, A):
+    A = np.ascontiguousarray(A, dtype=np.complex128)
+    n = A.shape[0]
+    er, ei, S, W = _exact_cplx(A)
+    mr, mi = _model_cplx2_sweep(A)
+    bound = Fraction(complex_sweep_bound(S, W, n))
+    assert abs(mr - er) <= bound and abs(mi - ei) <= bound, (name, float(abs(mr - er)), float(abs(mi - ei)),
+                                                             float(bound))
