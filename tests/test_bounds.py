@@ -7,29 +7,28 @@ rational arithmetic:
 
 * the exact range sum sum_g (-1)^g prod_i x_i(g) and the magnitude sums S and
   W are computed with Fractions (every binary64 entry is a dyadic rational);
-* the double-double oracle (ryser_dd_stats_range) must lie within
-  dd_oracle_bound of the exact sum and reproduce S and W;
-* the same for the complex double-double oracle (ryser_cdd_range) and
-  bit-level models of the complex sweeps (signed 62-bit limb products, the
-  larger part renormalised to 2^60): the one-lane layout (n < 16: two chains
-  and a merge) and the two-lane layout (n >= 16: one chain per lane over half
-  the rows, then a merge) against complex_sweep_bound, part by part;
-* a bit-level model of the sparse sweep in Alg. 2's column order (rows
-  without the odd unit, exact zeros skipped, the product of all rows merged
-  with two empty chains) against the same real_sweep_bound;
-* a bit-level model of the real gradient sweep (normalised leaves, the
-  exclusive butterfly over eight lanes, one rounding per term, binary64
-  prefix and column sums per chunk) against the derived 2^-42 S_k;
-* a bit-level model of the dense real sweep's fixed-point arithmetic (the
-  staging of every row, the odd last column, the 62-bit products with their
-  renormalising shifts, the exponent bookkeeping, and the integer assembly of
-  each term's binary64 head and tail, including a product chain that a factor
-  |Y_i| = 1 has emptied; Alg. 1's terms, summed exactly) must lie within
-  real_sweep_bound.  The model restates the integer operations the kernel
-  documents (two chains over even and odd rows and one merge per step) in
-  Python integers; it shares no code with the CUDA sources.  The
-  double-double accumulation of the terms (below 2^-64 S per chunk) is left
-  out; the bound's 2^-59 S allowance covers it.
+* the double-double oracles (ryser_dd_stats_range, ryser_cdd_range) must lie
+  within dd_oracle_bound of the exact sum and reproduce S and W;
+* bit-level models of the kernels' integer arithmetic must lie within the
+  bounds the GPU parity tests use.  Each model restates in Python integers
+  the operations its kernel documents and shares no code with the CUDA
+  sources; the double-double accumulation of the terms (below 2^-64 S per
+  chunk) is left out, the bounds' 2^-59 S allowance covers it:
+  - dense real (real_sweep_bound): the staging of every row, the odd last
+    column, two chains of 62-bit products over even and odd rows with their
+    renormalising shifts and one merge, the exponent bookkeeping, and the
+    integer assembly of each term's binary64 head and tail, including a chain
+    that a factor |Y_i| = 1 has emptied;
+  - sparse in Alg. 2's column order (real_sweep_bound): rows without the odd
+    unit, exact zeros skipped, the chain of all rows merged with two empty
+    chains;
+  - complex (complex_sweep_bound, part by part): signed 62-bit limb products
+    with the larger part renormalised to 2^60, in the one-lane layout
+    (n < 16: two chains and a merge) and the two-lane layout (n >= 16: one
+    chain per lane over half the rows, then a merge);
+  - the real gradient (2^-42 S_k): normalised leaves, the exclusive butterfly
+    over eight lanes, one rounding per term, binary64 prefix and column sums
+    inside each chunk.
 """
 import math
 from fractions import Fraction
